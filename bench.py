@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark: FMM evaluations/s (build + evaluate) and P2P Gpair/s at N = 1,048,576.
+
+Workload (the plain FP32 FMM on the GPU): N = 1,048,576 particles uniform in
+[0,1)^3 (FP64), charges uniform in [-1,1), Laplace potential + gradient,
+P = 4, theta = 0.4, ncrit = 64.  One step = fmm_build (keys, sort, tree,
+dual tree traversal, list grouping) + fmm_evaluate (P2M, M2M, M2L, L2L,
+P2P + L2P + scatter) with inputs resident in HBM; L2 is flushed (256 MiB
+write) before every timed step, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path does not shard (one FMM per GPU), so N GPUs run N
+independent replicas; value = all evaluations / max-over-ranks time.
+--impl reference times the CPU oracle (FP64 C) on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM evals/s & P2P Gpair/s at N=1M, rel err 1e-4, vs plain FP32 path"
+FLOPS_PER_PAIR = 20          # the paper's count for a potential + force interaction (Table 4)
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=1048576)
+    ap.add_argument("--P", type=int, default=4)
+    ap.add_argument("--theta", type=float, default=0.4)
+    ap.add_argument("--ncrit", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(N):
+    from paper_1209_3516_gb300 import inputs
+    return inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+
+
+def config(a):
+    return {"workload": "uniform cube N=%d, P=%d, theta=%.2f, ncrit=%d, potential+gradient, one charge vector"
+                        % (a.N, a.P, a.theta, a.ncrit),
+            "N": a.N, "P": a.P, "theta": a.theta, "ncrit": a.ncrit,
+            "step": "fmm_build + fmm_evaluate",
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(a, x, q):
+    """Particles of the workload in the octant [0, 1/2)^3: same density, same leaves."""
+    m = np.all(x < 0.5, axis=1)
+    return x[m], q[m]
+
+
+def time_oracle(a, xs, qs, reps=1):
+    import oracle
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        f = oracle.FMM(xs.shape[0], a.P, a.theta, a.ncrit).build(xs)
+        f.evaluate(qs)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def cpu_baseline(a, x, q, reps=1):
+    import oracle
+    xs, qs = oracle_sample(a, x, q)
+    ts = time_oracle(a, xs, qs, reps)
+    t_full = statistics.median(ts) * a.N / xs.shape[0]
+    return {"value": 1.0 / t_full, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "FP64 oracle FMM (build + evaluate, same P/theta/ncrit) on the %d particles of the "
+                      "workload in the octant [0,1/2)^3 (same density and leaves), time scaled by N/%d"
+                      % (xs.shape[0], xs.shape[0]),
+            "seconds_per_sample": statistics.median(ts)}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) == len(self.FIELDS):
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_id_for_smi(dev):
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis and "," not in vis:
+            return vis
+        return dev
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup(a):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if a.impl == "ours" and torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(a):
+    # under torchrun only rank 0 times the oracle; the other ranks exit without work
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    import oracle
+    x, q = workload(a.N)
+    xs, qs = oracle_sample(a, x, q)
+    time_oracle(a, xs, qs, reps=max(0, a.warmup))
+    t0 = time.perf_counter()
+    ts = time_oracle(a, xs, qs, reps=a.steps)
+    wall = time.perf_counter() - t0
+    scale = a.N / xs.shape[0]
+    per_eval = statistics.mean(ts) * scale
+    value = 1.0 / per_eval
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "evals/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "each step: FP64 oracle FMM (build + evaluate) on the %d particles of the "
+                                       "workload in [0,1/2)^3, time scaled by N/%d" % (xs.shape[0], xs.shape[0])},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(a):
+    import torch
+    from paper_1209_3516_gb300 import fmm
+
+    ws, rank, local, pg = dist_setup(a)
+    dev = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    x, q = workload(a.N)
+    q32 = q.astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q32).cuda()
+    phi = torch.empty(a.N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(a.N, 3, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, timing=True)
+
+    def step():
+        h.build(xd)
+        h.evaluate(qd, phi=phi, grad=grad)
+
+    for _ in range(a.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    launches0 = h.stats()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    p2p_ms, m2l_ms, phase_acc = [], [], {}
+    sampler = ClockSampler(gpu_id_for_smi(dev))
+    barrier(pg)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for k in range(a.steps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        st = h.stats()
+        p2p_ms.append(st["ms_phase"]["p2p"])
+        m2l_ms.append(st["ms_phase"]["m2l"])
+        for kk, vv in st["ms_phase"].items():
+            phase_acc.setdefault(kk, []).append(vv)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    st = h.stats()
+    launches = st["kernel_launches"] - launches0
+    total_ms_max = max_over_ranks(pg, total_ms)
+    value = ws * a.steps / (total_ms_max / 1e3)
+
+    # P2P kernel: algorithmic work per launch = particle pairs of the P2P list
+    pairs = st["p2p_pairs"]
+    p2p_mean = statistics.mean(p2p_ms)
+    gpair_s = pairs / (p2p_mean * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_PAIR / (p2p_mean * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "p2p_traffic.json")
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("N") == a.N and pj.get("P") == a.P and pj.get("theta") == a.theta and pj.get("ncrit") == a.ncrit:
+                traffic = pj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q32).pin_memory()
+    ph = torch.empty(a.N, dtype=torch.float32).pin_memory()
+    gh = torch.empty(a.N, 3, dtype=torch.float32).pin_memory()
+    xn, qn, pn, gn = xh.numpy(), qh.numpy(), ph.numpy(), gh.numpy()
+    h.evaluate_host(xn, qn, pn, gn)
+    e2e_ms = []
+    for _ in range(a.e2e_steps):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.evaluate_host(xn, qn, pn, gn)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_max = max_over_ranks(pg, sum(e2e_ms))
+    e2e_value = ws * a.e2e_steps / (e2e_max / 1e3)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(a),
+                "p2p_gpair_s": gpair_s,
+                "roofline": {"kernel": "k_p2p", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                             "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+                             "launch_ms": p2p_mean,
+                             "peak_basis": "%d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % (sms, sm_max)},
+                "phases_ms": {k: statistics.mean(v) for k, v in phase_acc.items()},
+                "counts": {"ncells": st["ncells"], "nleaves": st["nleaves"], "nlevels": st["nlevels"],
+                           "n_m2l": st["n_m2l"], "n_p2p": st["n_p2p"], "p2p_pairs": pairs},
+                "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": x.nbytes + q32.nbytes,
+                        "d2h_bytes_per_step": 4 * a.N * 4},
+                "gpu_launches": launches,
+                "clocks": clocks}
+        if not a.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(a, x, q)
+    h.close()
+    if line is not None:
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

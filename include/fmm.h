@@ -1,0 +1,204 @@
+/*
+ * fmm.h -- C ABI of the GB300 dual-tree-traversal FMM for the 3-D Laplace kernel.
+ *
+ * Method: R. Yokota, "An FMM Based on Dual Tree Traversal for Many-core
+ * Architectures" (arXiv:1209.3516).  The library computes, for N particles
+ * with positions x_i and charges q_i,
+ *     phi_i  = sum_{j : r_ij != 0} q_j / r_ij                  (potential)
+ *     grad_i = -sum_{j : r_ij != 0} q_j (x_i - x_j) / r_ij^3   (its gradient)
+ * (the Laplace kernel of Sec. 3.2 and Table 3; no 1/(4 pi), no softening), with
+ * an FMM whose interaction lists come from a dual tree traversal (Algorithms 3
+ * and 4) under the multipole acceptance criterion theta * R > B_A + B_B
+ * (Sec. 3.2), Cartesian Taylor expansions of order P (Sec. 3.1, Table 1), and
+ * leaves of at most ncrit particles (Table 3).  Accuracy is controlled by both
+ * P and theta (Sec. 3.2, Table 3).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int: FMM_OK (0) or a negative FMM_ERR_* code.  No
+ *     exception or abort crosses the ABI.  fmm_last_error_string() returns a
+ *     message for the last failing call of the calling thread.
+ *   - Unless a call says "host", every pointer argument is a DEVICE pointer
+ *     on the handle's device.  The caller owns all arrays it passes; the handle
+ *     owns all of its internal device workspaces.
+ *   - Work is issued asynchronously on the handle's stream (fmm_options.stream).
+ *     Calls that return sizes or host data synchronise that stream.
+ *   - A handle must not be used from two threads at the same time.
+ *   - Layouts: positions x are N x 3 row-major FP64 (x0 y0 z0 x1 y1 z1 ...);
+ *     charges q and potentials phi are N FP32; gradients grad are N x 3
+ *     row-major FP32.  All outputs are in the caller's particle order.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define FMM_OK 0
+#define FMM_ERR_ARG (-1)          /* null pointer, size or parameter out of range */
+#define FMM_ERR_UNSUPPORTED (-2)  /* expansion order P not compiled into the library */
+#define FMM_ERR_INPUT (-3)        /* a coordinate is NaN or infinite */
+#define FMM_ERR_CUDA (-4)         /* CUDA runtime error (see fmm_last_error_string) */
+#define FMM_ERR_NOMEM (-5)        /* device allocation failed */
+#define FMM_ERR_STATE (-6)        /* evaluate or query before a successful build */
+#define FMM_ERR_CAPACITY (-7)     /* a traversal buffer overflowed again after regrowing */
+
+/* Flags for fmm_options.flags. */
+#define FMM_FLAG_KAHAN 1u         /* compensated (Kahan) P2P accumulation per target */
+#define FMM_FLAG_TIMING 2u        /* record per-phase device times (adds events) */
+
+typedef struct fmm_handle fmm_handle;
+
+typedef struct fmm_options {
+    void *stream;      /* cudaStream_t to issue work on; NULL = the legacy default stream */
+    int device;        /* CUDA device ordinal; -1 = the current device */
+    unsigned flags;    /* FMM_FLAG_* */
+} fmm_options;
+
+/* Phase indices of fmm_stats.ms_phase (device times of the last build/evaluate). */
+enum {
+    FMM_PHASE_MORTON = 0,  /* bounding box, normalisation, Morton keys */
+    FMM_PHASE_SORT,        /* radix sort of (key, index) */
+    FMM_PHASE_TREE,        /* ncrit splitting, cell table, cell geometry */
+    FMM_PHASE_TRAVERSE,    /* dual tree traversal (seeding rounds + work-stack kernel) */
+    FMM_PHASE_LISTS,       /* grouping of the lists by target cell */
+    FMM_PHASE_UPWARD,      /* charge gather, P2M, M2M */
+    FMM_PHASE_M2L,
+    FMM_PHASE_DOWNWARD,    /* L2L */
+    FMM_PHASE_P2P,         /* P2P + L2P + output scatter */
+    FMM_NPHASES
+};
+
+/* Counters and timings (fmm_stats). */
+struct fmm_stats {
+    int64_t n;                  /* particles */
+    int64_t ncells, nleaves;    /* cells of the octree, leaves among them */
+    int32_t nlevels;            /* levels present (root = level 0) */
+    int32_t P;                  /* expansion order */
+    int64_t n_m2l, n_p2p;       /* cell pairs in the M2L and P2P lists */
+    int64_t p2p_pairs;          /* particle pairs of the P2P list: sum n_target * n_source */
+    double ms_build, ms_evaluate;          /* device time of the last build / evaluate */
+    double ms_phase[FMM_NPHASES];          /* per phase, when FMM_FLAG_TIMING is set */
+    int64_t kernel_launches;               /* CUDA kernels launched by this handle since creation */
+};
+
+/*
+ * fmm_create -- allocate a handle for N particles.
+ *   N      >= 1 particles.
+ *   P      expansion order: multipole and local expansions hold every Taylor
+ *          coefficient of total degree <= P-1 (Sec. 3.1; the error of one M2L is
+ *          of order ((B_A+B_B)/R)^P, Sec. 3.2).  Compiled orders: 3, 4, 5, 6, 8;
+ *          others give FMM_ERR_UNSUPPORTED.
+ *   theta  opening angle of the MAC, 0 <= theta < 1 (Sec. 3.2); theta = 0 accepts no
+ *          pair, so every interaction is a direct P2P sum.
+ *   ncrit  >= 1, the largest number of particles in a leaf (Table 3's N_crit);
+ *          a cell at the deepest level (21) stays a leaf whatever its size.
+ *   opt    may be NULL (default stream, current device, no flags).
+ * On success *h holds a new handle; on error *h is set to NULL.
+ */
+int fmm_create(fmm_handle **h, int64_t N, int P, float theta, int ncrit, const fmm_options *opt);
+
+/*
+ * fmm_build -- tree and interaction lists for the positions x (device, N x 3 FP64).
+ * Steps (each a GPU kernel, Sec. 3.3 and Table 2): bounding box and normalisation
+ * to the cube (-1,1)^3 in FP64, 63-bit Morton keys, stable radix sort of
+ * (key, index), level-by-level splitting of cells with more than ncrit particles
+ * into their non-empty octants, cell centres and tight radii, then the dual tree
+ * traversal (Algorithms 3 and 4) emitting the M2L and P2P cell-pair lists, which
+ * are grouped by target cell.  x is only read during the call; the handle keeps
+ * its own sorted copy.  Errors: FMM_ERR_INPUT for a NaN/Inf coordinate,
+ * FMM_ERR_CAPACITY if a traversal buffer overflows after one regrowth.
+ * Synchronises the stream (list sizes are read back).
+ */
+int fmm_build(fmm_handle *h, const double *x);
+
+/*
+ * fmm_evaluate -- potential and gradient at every particle.
+ *   x     the positions (device); if x differs from the pointer passed to the
+ *         last fmm_build, the tree is rebuilt first; NULL reuses the last build.
+ *   q     charges, device, N FP32.
+ *   phi   out, device, N FP32, or NULL if not wanted.
+ *   grad  out, device, N x 3 FP32, or NULL if not wanted (not both NULL).
+ * Steps: P2M, M2M (upward), M2L over the M2L list, L2L (downward), then one
+ * kernel doing P2P over the P2P list, L2P, and the scatter to caller order and
+ * physical units (phi / h, grad / h^2 for the normalisation scale h).
+ * Asynchronous on the handle's stream.
+ */
+int fmm_evaluate(fmm_handle *h, const double *x, const float *q, float *phi, float *grad);
+
+/*
+ * fmm_evaluate_host -- fmm_build + fmm_evaluate on HOST arrays: copies x (N x 3
+ * FP64) and q (N FP32) to the device, builds, evaluates, copies phi (N) and grad
+ * (N x 3) back.  phi or grad may be NULL.  Synchronous.
+ */
+int fmm_evaluate_host(fmm_handle *h, const double *x_host, const float *q_host, float *phi_host,
+                      float *grad_host);
+
+/*
+ * fmm_energy -- E = 1/2 sum_i q_i phi_i of the last evaluate, reduced in FP64 on
+ * the device.  E is a HOST pointer.  Synchronises the stream.
+ */
+int fmm_energy(fmm_handle *h, double *E);
+
+/*
+ * fmm_backward -- adjoint of the last evaluate for upstream gradients dphi
+ * (N FP32, may be NULL) and dgrad (N x 3 FP32, may be NULL) of a loss L(phi, grad).
+ *   dq  out (device, N FP32, may be NULL): dL/dq_j = sum_i dphi_i / r_ij
+ *       - sum_i dgrad_i . (x_i - x_j) / r_ij^3, i.e. the potential at x_j of the
+ *       charges dphi plus that of dipoles dgrad (the kernel is symmetric).
+ *   dx  out (device, N x 3 FP32, may be NULL): dL/dx_i.
+ * Returns FMM_ERR_UNSUPPORTED for the parts this build does not provide
+ * (see fmm_last_error_string).
+ */
+int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq, float *dx);
+
+/* fmm_stats -- counters and timings of the last build/evaluate into *s (HOST). */
+int fmm_stats(fmm_handle *h, struct fmm_stats *s);
+
+/* fmm_destroy -- free the handle and all its device memory (NULL is a no-op). */
+int fmm_destroy(fmm_handle *h);
+
+/* Message for the last failing call on this thread (static storage; never NULL). */
+const char *fmm_last_error_string(void);
+
+/* ---- Introspection (synchronous device -> HOST copies, for tests and tools) ---- */
+
+/*
+ * fmm_get_norm -- normalisation of the last build: u = (x - centre) / h.
+ * centre: HOST double[3]; h: HOST double.
+ */
+int fmm_get_norm(fmm_handle *h, double *centre, double *scale);
+
+/*
+ * fmm_get_sorted -- HOST arrays of length N: sorted Morton keys and perm
+ * (perm[s] = caller index of the s-th particle in key order).  Either may be NULL.
+ */
+int fmm_get_sorted(fmm_handle *h, uint64_t *keys, int32_t *perm);
+
+/* fmm_get_ncells -- number of cells of the last build (HOST out). */
+int fmm_get_ncells(fmm_handle *h, int64_t *ncells);
+
+/*
+ * fmm_get_cells -- HOST arrays of length ncells (breadth-first order), any may be NULL:
+ * canonical id (1 << 3*level) | Morton prefix, level, first sorted particle,
+ * particle count, number of children (0 = leaf), parent index (-1 for the root),
+ * centre (ncells x 3 FP32) and tight radius (FP32).
+ */
+int fmm_get_cells(fmm_handle *h, uint64_t *canon, int32_t *level, int32_t *pbeg, int32_t *pcnt,
+                  int32_t *nchild, int32_t *parent, float *centre, float *radius);
+
+/*
+ * fmm_get_lists -- list sizes (HOST n_m2l, n_p2p; either may be NULL) and, if the
+ * array pointers are non-NULL, the lists as HOST int32 (target, source) cell-index
+ * pairs, 2 x n each, grouped by target and sorted by (target, source).
+ */
+int fmm_get_lists(fmm_handle *h, int64_t *n_m2l, int64_t *n_p2p, int32_t *m2l, int32_t *p2p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

@@ -1,0 +1,458 @@
+// api.cu -- the C ABI (include/fmm.h): handles, build / evaluate orchestration,
+// host-buffer entry point, energy, counters and introspection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
+{
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+    g_last_error = buf;
+    return e == cudaErrorMemoryAllocation ? FMM_ERR_NOMEM : FMM_ERR_CUDA;
+}
+
+int DevBuf::reserve(size_t need)
+{
+    if (need <= bytes && p) return FMM_OK;
+    release();
+    size_t sz = std::max<size_t>(need, 256);
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+    bytes = sz;
+    return FMM_OK;
+}
+
+int DevBuf::reserve_keep(size_t need, cudaStream_t s)
+{
+    if (need <= bytes && p) return FMM_OK;
+    void *np = nullptr;
+    size_t sz = std::max<size_t>(need, 256);
+    cudaError_t e = cudaMalloc(&np, sz);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    if (p) {
+        e = cudaMemcpyAsync(np, p, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(np);
+            return cuda_fail(e, "regrow copy", __FILE__, __LINE__);
+        }
+        cudaFree(p);
+    }
+    p = np;
+    bytes = sz;
+    return FMM_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+void phase_begin(Handle &h, int phase)
+{
+    if (h.events_ready && (h.flags & FMM_FLAG_TIMING)) cudaEventRecord(h.ev[2 * phase], h.stream);
+}
+
+void phase_end(Handle &h, int phase)
+{
+    if (h.events_ready && (h.flags & FMM_FLAG_TIMING)) cudaEventRecord(h.ev[2 * phase + 1], h.stream);
+}
+
+static bool supported_order(int P) { return P == 3 || P == 4 || P == 5 || P == 6 || P == 8; }
+
+// Pins the handle's device for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+static int do_build(Handle &h, const double *x)
+{
+    h.built = false;
+    h.evaluated = false;
+    const int ev0 = 2 * kPhases, ev1 = 2 * kPhases + 1;
+    if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
+    FMM_TRY(build_keys(h, x));
+    FMM_TRY(build_tree(h));
+    FMM_TRY(build_lists(h));
+    FMM_TRY(build_p2p_items(h));
+    if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    if (h.events_ready) cudaEventElapsedTime(&h.ms_build, h.ev[ev0], h.ev[ev1]);
+    h.x_built = x;
+    h.built = true;
+    return FMM_OK;
+}
+
+static int do_evaluate(Handle &h, const float *q, float *phi, float *grad)
+{
+    const int ev0 = 2 * kPhases + 2, ev1 = 2 * kPhases + 3;
+    if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
+    phase_begin(h, FMM_PHASE_UPWARD);
+    FMM_TRY(evaluate_upward(h, q));
+    phase_end(h, FMM_PHASE_UPWARD);
+    phase_begin(h, FMM_PHASE_M2L);
+    FMM_TRY(evaluate_m2l(h));
+    phase_end(h, FMM_PHASE_M2L);
+    phase_begin(h, FMM_PHASE_DOWNWARD);
+    FMM_TRY(evaluate_downward(h));
+    phase_end(h, FMM_PHASE_DOWNWARD);
+    phase_begin(h, FMM_PHASE_P2P);
+    FMM_TRY(evaluate_p2p(h, phi, grad));
+    phase_end(h, FMM_PHASE_P2P);
+    if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
+    h.evaluated = true;
+    return FMM_OK;
+}
+
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+const char *fmm_last_error_string(void) { return g_last_error.c_str(); }
+
+int fmm_create(fmm_handle **hp, int64_t N, int P, float theta, int ncrit, const fmm_options *opt)
+{
+    if (!hp) {
+        set_error("fmm_create: null handle pointer");
+        return FMM_ERR_ARG;
+    }
+    *hp = nullptr;
+    if (N < 1 || N > 0x7fffffffll) {
+        set_error("fmm_create: N must be in [1, 2^31 - 1]");
+        return FMM_ERR_ARG;
+    }
+    if (!(theta >= 0.0f && theta < 1.0f)) {
+        set_error("fmm_create: theta must be in [0, 1)");
+        return FMM_ERR_ARG;
+    }
+    if (ncrit < 1) {
+        set_error("fmm_create: ncrit must be >= 1");
+        return FMM_ERR_ARG;
+    }
+    if (!supported_order(P)) {
+        set_error("fmm_create: expansion order P must be one of 3, 4, 5, 6, 8");
+        return FMM_ERR_UNSUPPORTED;
+    }
+    int dev = opt && opt->device >= 0 ? opt->device : -1;
+    if (dev < 0) FMM_CUDA(cudaGetDevice(&dev));
+    DeviceGuard guard(dev);
+    fmm_handle *w = new (std::nothrow) fmm_handle;
+    if (!w) {
+        set_error("fmm_create: out of host memory");
+        return FMM_ERR_NOMEM;
+    }
+    Handle &h = w->h;
+    h.N = N;
+    h.P = P;
+    h.TP = ((P * (P + 1) * (P + 2) / 6) + 3) & ~3;
+    h.theta = theta;
+    h.ncrit = ncrit;
+    h.flags = opt ? opt->flags : 0u;
+    h.device = dev;
+    h.stream = opt ? static_cast<cudaStream_t>(opt->stream) : nullptr;
+    cudaError_t e = cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h.pinned), sizeof(PinnedScratch));
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "fmm_create", __FILE__, __LINE__);
+        delete w;
+        return rc;
+    }
+    std::memset(h.pinned, 0, sizeof(PinnedScratch));
+    bool ok = true;
+    for (auto &ev : h.ev) ok = ok && cudaEventCreate(&ev) == cudaSuccess;
+    h.events_ready = ok;
+    *hp = w;
+    return FMM_OK;
+}
+
+int fmm_destroy(fmm_handle *w)
+{
+    if (!w) return FMM_OK;
+    Handle &h = w->h;
+    DeviceGuard guard(h.device);
+    if (h.stream) cudaStreamSynchronize(h.stream);
+    else cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&h.norm, &h.bbox_part, &h.err_flag, &h.keys, &h.keys_alt, &h.idx, &h.idx_alt, &h.sort_hist,
+                      &h.scan_tmp, &h.pos_unsorted, &h.pos, &h.perm, &h.c_prefix, &h.c_level, &h.c_pbeg, &h.c_pcnt,
+                      &h.c_cbeg, &h.c_ccnt, &h.c_parent, &h.c_geom, &h.c_kids, &h.c_r2bits, &h.c_tmp, &h.leaf_of,
+                      &h.counters, &h.front[0], &h.front[1], &h.m2l_raw, &h.p2p_raw, &h.lkeys, &h.lkeys_alt,
+                      &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_rng,
+                      &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad};
+    for (DevBuf *b : bufs) b->release();
+    if (h.events_ready)
+        for (auto &ev : h.ev) cudaEventDestroy(ev);
+    if (h.pinned) cudaFreeHost(h.pinned);
+    delete w;
+    return FMM_OK;
+}
+
+int fmm_build(fmm_handle *w, const double *x)
+{
+    if (!w || !x) {
+        set_error("fmm_build: null argument");
+        return FMM_ERR_ARG;
+    }
+    DeviceGuard guard(w->h.device);
+    return do_build(w->h, x);
+}
+
+int fmm_evaluate(fmm_handle *w, const double *x, const float *q, float *phi, float *grad)
+{
+    if (!w || !q || (!phi && !grad)) {
+        set_error("fmm_evaluate: null argument");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    DeviceGuard guard(h.device);
+    if (x && (!h.built || x != h.x_built)) FMM_TRY(do_build(h, x));
+    if (!h.built) {
+        set_error("fmm_evaluate: no tree (call fmm_build or pass x)");
+        return FMM_ERR_STATE;
+    }
+    return do_evaluate(h, q, phi, grad);
+}
+
+int fmm_evaluate_host(fmm_handle *w, const double *x_host, const float *q_host, float *phi_host, float *grad_host)
+{
+    if (!w || !x_host || !q_host || (!phi_host && !grad_host)) {
+        set_error("fmm_evaluate_host: null argument");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    DeviceGuard guard(h.device);
+    const int64_t N = h.N;
+    FMM_TRY(h.hx.reserve(N * 3 * sizeof(double)));
+    FMM_TRY(h.hq.reserve(N * sizeof(float)));
+    FMM_TRY(h.hphi.reserve(N * sizeof(float)));
+    FMM_TRY(h.hgrad.reserve(N * 3 * sizeof(float)));
+    FMM_CUDA(cudaMemcpyAsync(h.hx.p, x_host, N * 3 * sizeof(double), cudaMemcpyHostToDevice, h.stream));
+    FMM_CUDA(cudaMemcpyAsync(h.hq.p, q_host, N * sizeof(float), cudaMemcpyHostToDevice, h.stream));
+    FMM_TRY(do_build(h, h.hx.as<double>()));
+    FMM_TRY(do_evaluate(h, h.hq.as<float>(), phi_host ? h.hphi.as<float>() : nullptr,
+                        grad_host ? h.hgrad.as<float>() : nullptr));
+    if (phi_host)
+        FMM_CUDA(cudaMemcpyAsync(phi_host, h.hphi.p, N * sizeof(float), cudaMemcpyDeviceToHost, h.stream));
+    if (grad_host)
+        FMM_CUDA(cudaMemcpyAsync(grad_host, h.hgrad.p, N * 3 * sizeof(float), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    // the device copy of x is internal: a later fmm_evaluate(x = caller pointer) must rebuild
+    h.x_built = nullptr;
+    return FMM_OK;
+}
+
+int fmm_energy(fmm_handle *w, double *E)
+{
+    if (!w || !E) {
+        set_error("fmm_energy: null argument");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    if (!h.evaluated) {
+        set_error("fmm_energy: no evaluation yet");
+        return FMM_ERR_STATE;
+    }
+    DeviceGuard guard(h.device);
+    return energy_reduce(h, E);
+}
+
+int fmm_backward(fmm_handle *w, const float *dphi, const float *dgrad, float *dq, float *dx)
+{
+    (void)dphi;
+    (void)dgrad;
+    (void)dq;
+    (void)dx;
+    if (!w) {
+        set_error("fmm_backward: null handle");
+        return FMM_ERR_ARG;
+    }
+    set_error("fmm_backward: not available in this build");
+    return FMM_ERR_UNSUPPORTED;
+}
+
+int fmm_stats(fmm_handle *w, struct fmm_stats *s)
+{
+    if (!w || !s) {
+        set_error("fmm_stats: null argument");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    DeviceGuard guard(h.device);
+    std::memset(s, 0, sizeof(*s));
+    s->n = h.N;
+    s->ncells = h.ncells;
+    s->nleaves = h.nleaves;
+    s->nlevels = h.nlevels;
+    s->P = h.P;
+    s->n_m2l = h.n_m2l;
+    s->n_p2p = h.n_p2p;
+    s->p2p_pairs = h.p2p_pairs;
+    s->kernel_launches = h.launches;
+    if (h.events_ready) {
+        FMM_CUDA(cudaStreamSynchronize(h.stream));
+        s->ms_build = h.ms_build;
+        float ms = 0.f;
+        if (h.evaluated && cudaEventElapsedTime(&ms, h.ev[2 * kPhases + 2], h.ev[2 * kPhases + 3]) == cudaSuccess)
+            s->ms_evaluate = ms;
+        if (h.flags & FMM_FLAG_TIMING)
+            for (int p = 0; p < kPhases; ++p) {
+                ms = 0.f;
+                if (cudaEventElapsedTime(&ms, h.ev[2 * p], h.ev[2 * p + 1]) == cudaSuccess) s->ms_phase[p] = ms;
+            }
+        cudaGetLastError();   // an unrecorded phase event is not an error of this call
+    }
+    return FMM_OK;
+}
+
+int fmm_get_norm(fmm_handle *w, double *centre, double *scale)
+{
+    if (!w || !centre || !scale) {
+        set_error("fmm_get_norm: null argument");
+        return FMM_ERR_ARG;
+    }
+    if (!w->h.built) {
+        set_error("fmm_get_norm: no tree");
+        return FMM_ERR_STATE;
+    }
+    for (int a = 0; a < 3; ++a) centre[a] = w->h.norm_host[a];
+    *scale = w->h.norm_host[3];
+    return FMM_OK;
+}
+
+int fmm_get_sorted(fmm_handle *w, uint64_t *keys, int32_t *perm)
+{
+    if (!w) {
+        set_error("fmm_get_sorted: null handle");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    if (!h.built) {
+        set_error("fmm_get_sorted: no tree");
+        return FMM_ERR_STATE;
+    }
+    DeviceGuard guard(h.device);
+    if (keys) FMM_CUDA(cudaMemcpyAsync(keys, h.keys.p, h.N * sizeof(uint64_t), cudaMemcpyDeviceToHost, h.stream));
+    if (perm) FMM_CUDA(cudaMemcpyAsync(perm, h.perm.p, h.N * sizeof(int32_t), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    return FMM_OK;
+}
+
+int fmm_get_ncells(fmm_handle *w, int64_t *ncells)
+{
+    if (!w || !ncells) {
+        set_error("fmm_get_ncells: null argument");
+        return FMM_ERR_ARG;
+    }
+    if (!w->h.built) {
+        set_error("fmm_get_ncells: no tree");
+        return FMM_ERR_STATE;
+    }
+    *ncells = w->h.ncells;
+    return FMM_OK;
+}
+
+int fmm_get_cells(fmm_handle *w, uint64_t *canon, int32_t *level, int32_t *pbeg, int32_t *pcnt, int32_t *nchild,
+                  int32_t *parent, float *centre, float *radius)
+{
+    if (!w) {
+        set_error("fmm_get_cells: null handle");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    if (!h.built) {
+        set_error("fmm_get_cells: no tree");
+        return FMM_ERR_STATE;
+    }
+    DeviceGuard guard(h.device);
+    const int64_t nc = h.ncells;
+    auto cp = [&](void *dst, const DevBuf &b, size_t bytes) -> int {
+        if (!dst) return FMM_OK;
+        FMM_CUDA(cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToHost, h.stream));
+        return FMM_OK;
+    };
+    std::vector<int32_t> lev(nc);
+    std::vector<uint64_t> pre(canon ? nc : 0);
+    FMM_TRY(cp(lev.data(), h.c_level, nc * sizeof(int32_t)));
+    if (canon) FMM_TRY(cp(pre.data(), h.c_prefix, nc * sizeof(uint64_t)));
+    FMM_TRY(cp(pbeg, h.c_pbeg, nc * sizeof(int32_t)));
+    FMM_TRY(cp(pcnt, h.c_pcnt, nc * sizeof(int32_t)));
+    FMM_TRY(cp(nchild, h.c_ccnt, nc * sizeof(int32_t)));
+    FMM_TRY(cp(parent, h.c_parent, nc * sizeof(int32_t)));
+    std::vector<float4> geom((centre || radius) ? nc : 0);
+    if (centre || radius) FMM_TRY(cp(geom.data(), h.c_geom, nc * sizeof(float4)));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    for (int64_t c = 0; c < nc; ++c) {
+        if (level) level[c] = lev[c];
+        if (canon) canon[c] = (1ull << (3 * lev[c])) | pre[c];
+        if (centre) {
+            centre[3 * c + 0] = geom[c].x;
+            centre[3 * c + 1] = geom[c].y;
+            centre[3 * c + 2] = geom[c].z;
+        }
+        if (radius) radius[c] = geom[c].w;
+    }
+    return FMM_OK;
+}
+
+int fmm_get_lists(fmm_handle *w, int64_t *n_m2l, int64_t *n_p2p, int32_t *m2l, int32_t *p2p)
+{
+    if (!w) {
+        set_error("fmm_get_lists: null handle");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    if (!h.built) {
+        set_error("fmm_get_lists: no tree");
+        return FMM_ERR_STATE;
+    }
+    DeviceGuard guard(h.device);
+    if (n_m2l) *n_m2l = h.n_m2l;
+    if (n_p2p) *n_p2p = h.n_p2p;
+    const int64_t nc = h.ncells;
+    auto expand = [&](int32_t *out, const DevBuf &src, const DevBuf &off, int64_t n) -> int {
+        if (!out) return FMM_OK;
+        std::vector<int32_t> s(n), o(nc + 1);
+        if (n) FMM_CUDA(cudaMemcpyAsync(s.data(), src.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h.stream));
+        FMM_CUDA(cudaMemcpyAsync(o.data(), off.p, (nc + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, h.stream));
+        FMM_CUDA(cudaStreamSynchronize(h.stream));
+        for (int64_t c = 0; c < nc; ++c)
+            for (int32_t e = o[c]; e < o[c + 1]; ++e) {
+                out[2 * (int64_t)e] = (int32_t)c;
+                out[2 * (int64_t)e + 1] = s[e];
+            }
+        return FMM_OK;
+    };
+    FMM_TRY(expand(m2l, h.m2l_src, h.m2l_off, h.n_m2l));
+    FMM_TRY(expand(p2p, h.p2p_src, h.p2p_off, h.n_p2p));
+    return FMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// fmm_internal.cuh -- internal declarations of the GB300 DTT-FMM library.
+//
+// Data layout in HBM (all owned by the handle):
+//   particles  : float4 pos[N] in Morton order, (u_x, u_y, u_z, q) with u the
+//                position normalised to (-1,1)^3, rounded to FP32; perm[N] int32
+//                maps sorted slot -> caller index.
+//   cells      : breadth-first order (level by level, Morton order inside a
+//                level).  Structure-of-arrays: prefix (u64), level, pbeg,
+//                pcnt, cbeg, ccnt, parent (int32), geom float4 (centre, radius).
+//   lists      : int32 source cell ids grouped by target (CSR offsets per cell).
+//   expansions : M and L, ncells x TP floats (TP = coefficients padded to 4).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+constexpr int kLevels = 21;     // 3 * 21 = 63 Morton bits (Sec. 2: 21 levels per 64-bit key)
+constexpr int kPhases = FMM_NPHASES;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define FMM_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::fmm::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define FMM_CHECK_LAUNCH(what)                                                \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return ::fmm::cuda_fail(e_, what, __FILE__, __LINE__); \
+    } while (0)
+
+#define FMM_TRY(expr)                                                         \
+    do {                                                                      \
+        int r_ = (expr);                                                      \
+        if (r_ != FMM_OK) return r_;                                          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// growable device buffer
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int reserve(size_t need);        // grows (contents discarded), never shrinks
+    int reserve_keep(size_t need, cudaStream_t s);   // grows keeping contents
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Device-side counters of the traversal (one struct, zeroed per traversal).
+struct TravCounters {
+    unsigned long long n_m2l;     // pairs emitted to the M2L list
+    unsigned long long n_p2p;     // pairs emitted to the P2P list
+    unsigned long long n_next;    // pairs pushed to the next frontier / spill list
+    unsigned long long seed_next; // work-stack kernel: next seed to claim
+    unsigned long long p2p_pairs; // sum over P2P pairs of n_target * n_source
+    unsigned int overflow;        // bit 0: m2l, bit 1: p2p, bit 2: frontier/spill
+    unsigned int nleaves;         // leaves found by the leaf-list kernel
+};
+
+// Page-locked host scratch of a handle (counters read back during a build).
+struct PinnedScratch {
+    TravCounters ctr;
+    int2 root_kids;
+    unsigned level_total;
+    unsigned err;
+};
+
+struct Handle {
+    // configuration
+    int64_t N = 0;
+    int P = 0, TP = 0, ncrit = 0;
+    float theta = 0.f;
+    unsigned flags = 0;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    PinnedScratch *pinned = nullptr;   // page-locked host scratch
+
+    // build state
+    const double *x_built = nullptr;
+    bool built = false;
+    bool evaluated = false;
+    double norm_host[4] = {0, 0, 0, 1};   // centre xyz, h
+
+    // normalisation / keys / sort
+    DevBuf norm;          // double[4] + bbox partials
+    DevBuf bbox_part;     // double[nblocks * 6]
+    DevBuf err_flag;      // unsigned int: bit 0 = non-finite input
+    DevBuf keys, keys_alt;        // u64[N]
+    DevBuf idx, idx_alt;          // u32[N]
+    DevBuf sort_hist;             // u32[256 * tiles]
+    DevBuf scan_tmp;              // u32 scratch of the device-wide scan
+    DevBuf pos_unsorted;          // float4[N]
+    DevBuf pos;                   // float4[N] sorted (u, q)
+    DevBuf perm;                  // int32[N]
+
+    // cells
+    int64_t ncells = 0, nleaves = 0, cell_cap = 0;
+    int nlevels = 0;
+    std::vector<int64_t> level_off;   // host: first cell of each level, size nlevels + 1
+    DevBuf c_prefix;      // u64
+    DevBuf c_level, c_pbeg, c_pcnt, c_cbeg, c_ccnt, c_parent;   // int32
+    DevBuf c_geom;        // float4 (centre, radius)
+    DevBuf c_kids;        // int2 (first child, child count) for the traversal
+    DevBuf c_r2bits;      // u32 max squared radius (bits) during the build
+    DevBuf c_tmp;         // int32 per-cell scratch (child counts / offsets)
+    DevBuf leaf_of;       // int32[N] leaf of each sorted particle
+
+    // traversal
+    DevBuf counters;      // TravCounters
+    DevBuf front[2];      // int2 frontier / seed / spill arrays
+    int64_t front_cap = 0;
+    DevBuf m2l_raw, p2p_raw;   // int2 pairs as emitted
+    int64_t m2l_cap = 0, p2p_cap = 0;
+    int64_t n_m2l = 0, n_p2p = 0, p2p_pairs = 0;
+    // grouped lists
+    DevBuf lkeys, lkeys_alt;   // u64 packed (target << 32 | source) for grouping
+    DevBuf m2l_src, m2l_off;   // int32 sources, CSR offsets (ncells + 1)
+    DevBuf p2p_src, p2p_off;
+    DevBuf leaf_list;          // int32 leaf cell ids
+    DevBuf p2p_items;          // int4 (leaf, first target, target count, 0) work items of the P2P kernel
+    DevBuf p2p_rng;            // int2 (first particle, count) per P2P list entry
+    int64_t n_items = 0;
+    DevBuf pairs_count;        // u64 scratch (P2P particle-pair count)
+
+    // expansions and outputs
+    DevBuf M, L;          // float[ncells * TP]
+    DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
+    DevBuf energy_part;   // double partials
+
+    // host-side scratch for the host-buffer entry point
+    DevBuf hx, hq, hphi, hgrad;
+
+    // kernel launches issued by this handle (all phases, since creation)
+    int64_t launches = 0;
+
+    // timing
+    cudaEvent_t ev[2 * kPhases + 4] = {};
+    bool events_ready = false;
+    float ms_phase[kPhases] = {};
+    float ms_build = 0.f, ms_eval = 0.f;
+};
+
+// ---------------------------------------------------------------------------
+// phases (implemented in the .cu files)
+// ---------------------------------------------------------------------------
+int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, unsigned *total_dev);
+int radix_sort_pairs(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals,
+                     unsigned *&vals_alt, int64_t n, int begin_bit, int end_bit);
+int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, int begin_bit,
+                    int end_bit);
+
+int build_keys(Handle &h, const double *x);       // bbox, normalise, Morton, sort, gather
+int build_tree(Handle &h);                        // cells, geometry
+int build_lists(Handle &h);                       // DTT + grouping
+int build_p2p_items(Handle &h);                   // P2P work items and source ranges
+
+int evaluate_upward(Handle &h, const float *q);   // gather q, P2M, M2M
+int evaluate_m2l(Handle &h);
+int evaluate_downward(Handle &h);                 // L2L
+int evaluate_p2p(Handle &h, float *phi, float *grad);   // P2P + L2P + scatter
+int energy_reduce(Handle &h, double *E);
+
+// phase timing helpers
+void phase_begin(Handle &h, int phase);
+void phase_end(Handle &h, int phase);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace fmm
+
+struct fmm_handle {
+    fmm::Handle h;
+};

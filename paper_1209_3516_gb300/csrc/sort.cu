@@ -1,0 +1,259 @@
+// sort.cu -- device-wide exclusive scan and LSD radix sort (64-bit keys).
+//
+// The radix sort orders the Morton keys of the particles (stable, so equal keys
+// keep the caller's order: the octree of Table 2 is "Morton key" based) and
+// groups the interaction lists by target cell.  Each 8-bit pass is three
+// kernels: a per-tile digit histogram, a device-wide exclusive scan of the
+// histograms in digit-major order, and a stable scatter whose in-tile ranks
+// come from __match_any_sync peer groups.
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 values per block
+
+// Exclusive scan across the block (blockDim.x a multiple of 32, at most 1024).
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *total)
+{
+    __shared__ unsigned warp_tot[32];
+    __shared__ unsigned block_tot;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned w = (int)lane < nw ? warp_tot[lane] : 0u;
+        unsigned wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned t = __shfl_up_sync(kFull, wi, o);
+            if ((int)lane >= o) wi += t;
+        }
+        if ((int)lane < nw) warp_tot[lane] = wi - w;
+        if (lane == 31) block_tot = wi;
+    }
+    __syncthreads();
+    unsigned res = incl - v + warp_tot[warp];
+    if (total) *total = block_tot;
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_reduce(const unsigned *in, int64_t n, unsigned *block_sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    s = warp_sum(s);
+    __shared__ unsigned ws[kScanThreads / 32];
+    if (lane_id() == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned t = threadIdx.x < kScanThreads / 32 ? ws[threadIdx.x] : 0u;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
+    }
+}
+
+// Single block: exclusive scan of nb block sums in place, total to *total.
+__global__ void k_scan_blocks(unsigned *sums, int nb, unsigned *total)
+{
+    unsigned carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        int i = base + threadIdx.x;
+        unsigned v = i < nb ? sums[i] : 0u;
+        unsigned tot;
+        unsigned ex = block_exclusive_scan(v, &tot);
+        if (i < nb) sums[i] = ex + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_apply(const unsigned *in, int64_t n, const unsigned *block_off, unsigned *out)
+{
+    __shared__ unsigned tile[kScanChunk];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        tile[k * kScanThreads + threadIdx.x] = i < n ? in[i] : 0u;
+    }
+    __syncthreads();
+    unsigned loc[kScanItems];
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = s;
+        s += tile[threadIdx.x * kScanItems + k];
+    }
+    unsigned ex = block_exclusive_scan(s, nullptr) + block_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) tile[threadIdx.x * kScanItems + k] = ex + loc[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = tile[k * kScanThreads + threadIdx.x];
+    }
+}
+
+int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, unsigned *total_dev)
+{
+    if (n <= 0) {
+        if (total_dev) FMM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(unsigned), h.stream));
+        return FMM_OK;
+    }
+    const int nb = ceil_div(n, kScanChunk);
+    FMM_TRY(h.scan_tmp.reserve((size_t)(nb + 1) * sizeof(unsigned)));
+    unsigned *sums = h.scan_tmp.as<unsigned>();
+    ++h.launches;
+    k_scan_reduce<<<nb, kScanThreads, 0, h.stream>>>(in, n, sums);
+    ++h.launches;
+    k_scan_blocks<<<1, kScanThreads, 0, h.stream>>>(sums, nb, total_dev);
+    ++h.launches;
+    k_scan_apply<<<nb, kScanThreads, 0, h.stream>>>(in, n, sums, out);
+    FMM_CHECK_LAUNCH("scan");
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits
+// ---------------------------------------------------------------------------
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsRounds = 16;
+constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per tile
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const uint64_t *keys, int64_t n, int shift, int ntiles,
+                                                           unsigned *hist)
+{
+    __shared__ unsigned cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int r = 0; r < kRsRounds; ++r) {
+        int64_t i = base + r * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+template <bool kVals>
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *keys, const unsigned *vals, int64_t n,
+                                                           int shift, int ntiles, const unsigned *offsets,
+                                                           uint64_t *keys_out, unsigned *vals_out)
+{
+    __shared__ unsigned s_base[256];
+    __shared__ unsigned s_cnt[kRsWarps][256];
+    const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    s_base[t] = offsets[(int64_t)t * ntiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) s_cnt[w][t] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsRounds; ++r) {
+        const int64_t i = base + r * kRsThreads + t;
+        const bool valid = i < n;
+        uint64_t key = valid ? keys[i] : 0ull;
+        unsigned val = 0;
+        if (kVals && valid) val = vals[i];
+        const unsigned d = valid ? ((unsigned)(key >> shift) & 0xffu) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
+        __syncthreads();
+        unsigned run = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) {
+            unsigned c = s_cnt[w][t];
+            s_cnt[w][t] = run;
+            run += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned pos = s_base[d] + s_cnt[warp][d] + rank;
+            keys_out[pos] = key;
+            if (kVals) vals_out[pos] = val;
+        }
+        __syncthreads();
+        s_base[t] += run;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) s_cnt[w][t] = 0;
+        __syncthreads();
+    }
+}
+
+static int radix_sort_impl(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals,
+                           unsigned *&vals_alt, bool with_vals, int64_t n, int begin_bit, int end_bit)
+{
+    if (n <= 1 || end_bit <= begin_bit) return FMM_OK;
+    if (n > 0xffffffffll) {
+        set_error("radix sort: more than 2^32 keys");
+        return FMM_ERR_ARG;
+    }
+    const int ntiles = ceil_div(n, kRsTile);
+    const int64_t nh = (int64_t)256 * ntiles;
+    FMM_TRY(h.sort_hist.reserve((size_t)nh * 2 * sizeof(unsigned)));
+    unsigned *hist = h.sort_hist.as<unsigned>();
+    unsigned *offs = hist + nh;
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+        ++h.launches;
+        k_rs_upsweep<<<ntiles, kRsThreads, 0, h.stream>>>(keys, n, shift, ntiles, hist);
+        FMM_CHECK_LAUNCH("radix upsweep");
+        FMM_TRY(scan_exclusive_u32(h, hist, offs, nh, nullptr));
+        if (with_vals) {
+            ++h.launches;
+            k_rs_scatter<true><<<ntiles, kRsThreads, 0, h.stream>>>(keys, vals, n, shift, ntiles, offs, keys_alt,
+                                                                  vals_alt);
+        } else {
+            ++h.launches;
+            k_rs_scatter<false><<<ntiles, kRsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ntiles, offs,
+                                                                   keys_alt, nullptr);
+        }
+        FMM_CHECK_LAUNCH("radix scatter");
+        uint64_t *tk = keys;
+        keys = keys_alt;
+        keys_alt = tk;
+        if (with_vals) {
+            unsigned *tv = vals;
+            vals = vals_alt;
+            vals_alt = tv;
+        }
+    }
+    return FMM_OK;
+}
+
+int radix_sort_pairs(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals, unsigned *&vals_alt,
+                     int64_t n, int begin_bit, int end_bit)
+{
+    return radix_sort_impl(h, keys, keys_alt, vals, vals_alt, true, n, begin_bit, end_bit);
+}
+
+int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, int begin_bit, int end_bit)
+{
+    unsigned *a = nullptr, *b = nullptr;
+    return radix_sort_impl(h, keys, keys_alt, a, b, false, n, begin_bit, end_bit);
+}
+
+}  // namespace fmm

@@ -1,0 +1,376 @@
+// traverse.cu -- dual tree traversal (Algorithms 3 and 4) and list grouping.
+//
+// Algorithm 3: pop a pair (A, B); split the larger cell (A when B is a leaf,
+// or when A is not a leaf and B_A > B_B; otherwise B, so ties split the source);
+// Algorithm 4 for every child pair: both leaves -> P2P, MAC -> M2L, else push.
+// MAC (Sec. 3.2): theta * |X_A - X_B| > B_A + B_B, in FP32 with one rounding
+// per operation (the same decision an FP32 implementation of the definition
+// takes).  The paper runs the traversal as tasks (TBB / OpenMP 3.0, Sec. 3.3);
+// here it runs in two GPU stages:
+//   1. breadth-first seeding rounds: one thread per (pair, child), until the
+//      frontier holds a few pairs per warp of the device;
+//   2. a persistent kernel: each warp claims seeds with an atomic counter and
+//      runs the traversal below each seed depth first on a private stack in
+//      shared memory, four pairs (32 child pairs) per step.  A warp whose stack
+//      is full spills the pushes to global memory; spilled pairs seed another
+//      launch.  No warp ever waits on another.
+// The emitted (target, source) pairs are then sorted by (target, source) so
+// that every target cell owns a contiguous, ordered run of sources.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_util.cuh"
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+constexpr unsigned kOvM2L = 1u, kOvP2P = 2u, kOvNext = 4u;
+constexpr int kStackCap = 256;      // pairs per warp stack
+constexpr int kStackWarps = 8;      // warps per block of the work-stack kernel
+
+struct Cell {
+    float4 g;   // centre, radius
+    int2 k;     // first child, child count (0 = leaf)
+};
+
+__device__ __forceinline__ Cell load_cell(const float4 *geom, const int2 *kids, int c)
+{
+    Cell r;
+    r.g = geom[c];
+    r.k = kids[c];
+    return r;
+}
+
+// Algorithm 4 outcome for the pair (a, b): 1 = P2P, 2 = M2L, 3 = push.
+__device__ __forceinline__ int interact(const Cell &a, const Cell &b, float theta)
+{
+    if (a.k.y == 0 && b.k.y == 0) return 1;
+    const float dx = __fsub_rn(a.g.x, b.g.x), dy = __fsub_rn(a.g.y, b.g.y), dz = __fsub_rn(a.g.z, b.g.z);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    const float R = __fsqrt_rn(r2);
+    return __fmul_rn(theta, R) > __fadd_rn(a.g.w, b.g.w) ? 2 : 3;
+}
+
+// Algorithm 3 split rule: true = split the target A.
+__device__ __forceinline__ bool split_target(const Cell &A, const Cell &B)
+{
+    return B.k.y == 0 || (A.k.y != 0 && A.g.w > B.g.w);
+}
+
+struct TravArgs {
+    const float4 *geom;
+    const int2 *kids;
+    float theta;
+    int2 *m2l;
+    unsigned long long m2l_cap;
+    int2 *p2p;
+    unsigned long long p2p_cap;
+    int2 *next;
+    unsigned long long next_cap;
+    TravCounters *ctr;
+};
+
+// Child pair j (0..7) of a popped pair; returns false when the split cell has fewer children.
+__device__ __forceinline__ bool child_pair(const TravArgs &a, int2 pr, int j, int2 &np, Cell &ca, Cell &cb)
+{
+    const Cell A = load_cell(a.geom, a.kids, pr.x);
+    const Cell B = load_cell(a.geom, a.kids, pr.y);
+    if (split_target(A, B)) {
+        if (j >= A.k.y) return false;
+        np = make_int2(A.k.x + j, pr.y);
+        ca = load_cell(a.geom, a.kids, np.x);
+        cb = B;
+    } else {
+        if (j >= B.k.y) return false;
+        np = make_int2(pr.x, B.k.x + j);
+        ca = A;
+        cb = load_cell(a.geom, a.kids, np.y);
+    }
+    return true;
+}
+
+// Seeding round: one thread per (frontier pair, child slot).
+__global__ void k_dtt_round(const int2 *front, unsigned long long nfront, TravArgs a)
+{
+    const unsigned long long total = nfront * 8ull;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (unsigned long long base = w0 * 32ull; base < total; base += nwarps * 32ull) {
+        const unsigned long long t = base + lane_id();
+        int kind = 0;
+        int2 np = make_int2(0, 0);
+        if (t < total) {
+            Cell ca, cb;
+            if (child_pair(a, front[t >> 3], (int)(t & 7ull), np, ca, cb)) kind = interact(ca, cb, a.theta);
+        }
+        warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
+        warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
+        warp_append(kind == 3, np, a.next, a.next_cap, &a.ctr->n_next, &a.ctr->overflow, kOvNext);
+    }
+}
+
+// Persistent work-stack kernel.
+__global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seeds, unsigned long long nseeds,
+                                                                TravArgs a)
+{
+    __shared__ int2 stack[kStackWarps][kStackCap];
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    int2 *st = stack[w];
+    int top = 0;
+    for (;;) {
+        if (top == 0) {
+            unsigned long long s = 0;
+            if (lane == 0) s = atomicAdd(&a.ctr->seed_next, 1ull);
+            s = __shfl_sync(kFull, s, 0);
+            if (s >= nseeds) break;
+            if (lane == 0) st[0] = seeds[s];
+            top = 1;
+            __syncwarp();
+        }
+        const int npop = min(top, 4);
+        top -= npop;
+        const int p = (int)(lane >> 3), j = (int)(lane & 7u);
+        int kind = 0;
+        int2 np = make_int2(0, 0);
+        int2 pr = make_int2(0, 0);
+        if (p < npop) pr = st[top + p];
+        __syncwarp();   // every popped entry is read before pushes overwrite the slots
+        if (p < npop) {
+            Cell ca, cb;
+            if (child_pair(a, pr, j, np, ca, cb)) kind = interact(ca, cb, a.theta);
+        }
+        warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
+        warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
+        const unsigned push = __ballot_sync(kFull, kind == 3);
+        const int npush = __popc(push);
+        if (top + npush <= kStackCap) {
+            if (kind == 3) st[top + __popc(push & lanemask_lt())] = np;
+            top += npush;
+        } else {
+            warp_append(kind == 3, np, a.next, a.next_cap, &a.ctr->n_next, &a.ctr->overflow, kOvNext);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// list grouping
+// ---------------------------------------------------------------------------
+__global__ void k_pack_pairs(const int2 *pairs, int64_t n, int cbits, uint64_t *keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = pairs[i];
+    keys[i] = ((uint64_t)(unsigned)p.x << cbits) | (uint64_t)(unsigned)p.y;
+}
+
+__global__ void k_unpack_sources(const uint64_t *keys, int64_t n, int cbits, int *src)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    src[i] = (int)(keys[i] & ((1ull << cbits) - 1ull));
+}
+
+// off[c] = first entry whose target is >= c, for c = 0..ncells.
+__global__ void k_csr_offsets(const uint64_t *keys, int64_t n, int cbits, int ncells, int *off)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncells) return;
+    const uint64_t v = (uint64_t)c << cbits;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    off[c] = (int)lo;
+}
+
+__global__ void k_pack_kids(int nc, const int *cbeg, const int *ccnt, int2 *kids)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nc) kids[c] = make_int2(cbeg[c], ccnt[c]);
+}
+
+// Leaves in cell order, and the P2P particle-pair count sum n_T * n_S.
+__global__ void k_leaf_list(int nc, const int *ccnt, int *leaf_list, unsigned *nleaves)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool leaf = c < nc && ccnt[c] == 0;
+    const unsigned m = __ballot_sync(kFull, leaf);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(nleaves, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (leaf) leaf_list[base + __popc(m & lanemask_lt())] = c;
+}
+
+__global__ void k_p2p_pairs(const int2 *pairs, int64_t n, const int *pcnt, unsigned long long *total)
+{
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = pairs[i];
+        s += (unsigned long long)pcnt[p.x] * (unsigned long long)pcnt[p.y];
+    }
+    s = warp_sum(s);
+    if (lane_id() == 0 && s) atomicAdd(total, s);
+}
+
+static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
+{
+    const int nc = (int)h.ncells;
+    int cbits = 1;
+    while ((1ll << cbits) <= nc) ++cbits;
+    FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(uint64_t)));
+    FMM_TRY(h.lkeys_alt.reserve(std::max<int64_t>(n, 1) * sizeof(uint64_t)));
+    FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
+    FMM_TRY(off.reserve((size_t)(nc + 1) * sizeof(int)));
+    if (n > 0) {
+        ++h.launches;
+        k_pack_pairs<<<ceil_div(n, 256), 256, 0, h.stream>>>(pairs, n, cbits, h.lkeys.as<uint64_t>());
+        uint64_t *k = h.lkeys.as<uint64_t>(), *ka = h.lkeys_alt.as<uint64_t>();
+        FMM_TRY(radix_sort_keys(h, k, ka, n, 0, 2 * cbits));
+        if (k != h.lkeys.as<uint64_t>()) std::swap(h.lkeys, h.lkeys_alt); {
+        ++h.launches;
+        k_unpack_sources<<<ceil_div(n, 256), 256, 0, h.stream>>>(h.lkeys.as<uint64_t>(), n, cbits, src.as<int>());
+        }
+    }
+    ++h.launches;
+    k_csr_offsets<<<ceil_div(nc + 1, 256), 256, 0, h.stream>>>(h.lkeys.as<uint64_t>(), n, cbits, nc, off.as<int>());
+    FMM_CHECK_LAUNCH("group list");
+    return FMM_OK;
+}
+
+int build_lists(Handle &h)
+{
+    const int nc = (int)h.ncells;
+    FMM_TRY(h.c_kids.reserve(nc * sizeof(int2)));
+    ++h.launches;
+    k_pack_kids<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
+                                                         h.c_kids.as<int2>());
+    FMM_TRY(h.counters.reserve(sizeof(TravCounters)));
+    TravCounters *ctr = h.counters.as<TravCounters>();
+    TravCounters *hc = &h.pinned->ctr;
+
+    // leaf list (all leaves, in cell order)
+    FMM_TRY(h.leaf_list.reserve(nc * sizeof(int)));
+    FMM_CUDA(cudaMemsetAsync(ctr, 0, sizeof(TravCounters), h.stream));
+    ++h.launches;
+    k_leaf_list<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_ccnt.as<int>(), h.leaf_list.as<int>(),
+                                                         &ctr->nleaves);
+    FMM_CHECK_LAUNCH("leaf list");
+
+    phase_begin(h, FMM_PHASE_TRAVERSE);
+    if (h.m2l_cap == 0) {
+        h.m2l_cap = (int64_t)nc * 64 + 1024;
+        h.p2p_cap = (int64_t)nc * 32 + 1024;
+        h.front_cap = (int64_t)nc * 8 + 4096;
+    }
+    const int seed_target = h.num_sms * 4 * kStackWarps * 8;   // about 8 seeds per resident warp
+    for (int attempt = 0;; ++attempt) {
+        FMM_TRY(h.m2l_raw.reserve(h.m2l_cap * sizeof(int2)));
+        FMM_TRY(h.p2p_raw.reserve(h.p2p_cap * sizeof(int2)));
+        FMM_TRY(h.front[0].reserve(h.front_cap * sizeof(int2)));
+        FMM_TRY(h.front[1].reserve(h.front_cap * sizeof(int2)));
+        FMM_CUDA(cudaMemsetAsync(ctr, 0, offsetof(TravCounters, nleaves), h.stream));
+        TravArgs a;
+        a.geom = h.c_geom.as<float4>();
+        a.kids = h.c_kids.as<int2>();
+        a.theta = h.theta;
+        a.m2l = h.m2l_raw.as<int2>();
+        a.m2l_cap = h.m2l_cap;
+        a.p2p = h.p2p_raw.as<int2>();
+        a.p2p_cap = h.p2p_cap;
+        a.next_cap = h.front_cap;
+        a.ctr = ctr;
+        int cur = 0;
+        unsigned long long nfront = 0;
+        bool overflow = false;
+        // the root pair (a root leaf is its own single P2P pair)
+        {
+            int2 root = make_int2(0, 0);
+            FMM_CUDA(cudaMemcpyAsync(h.front[0].p, &root, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
+            FMM_CUDA(cudaMemcpyAsync(&h.pinned->root_kids, h.c_kids.p, sizeof(int2), cudaMemcpyDeviceToHost,
+                                     h.stream));
+            FMM_CUDA(cudaStreamSynchronize(h.stream));
+        }
+        if (h.pinned->root_kids.y == 0) {
+            int2 rp = make_int2(0, 0);
+            FMM_CUDA(cudaMemcpyAsync(h.p2p_raw.p, &rp, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
+            FMM_CUDA(cudaStreamSynchronize(h.stream));
+            h.n_m2l = 0;
+            h.n_p2p = 1;
+            break;
+        }
+        nfront = 1;
+        // 1. seeding rounds
+        while (nfront > 0 && nfront < (unsigned long long)seed_target) {
+            a.next = h.front[cur ^ 1].as<int2>();
+            FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, sizeof(unsigned long long), h.stream));
+            const int blocks = (int)std::min<unsigned long long>((nfront * 8 + 255) / 256, (unsigned long long)h.num_sms * 16);
+            ++h.launches;
+            k_dtt_round<<<blocks, 256, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
+            FMM_CHECK_LAUNCH("dtt round");
+            FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
+            FMM_CUDA(cudaStreamSynchronize(h.stream));
+            if (hc->overflow) {
+                overflow = true;
+                break;
+            }
+            nfront = hc->n_next;
+            cur ^= 1;
+        }
+        // 2. work-stack kernel, relaunched on spilled pairs
+        while (!overflow && nfront > 0) {
+            a.next = h.front[cur ^ 1].as<int2>();
+            FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, 2 * sizeof(unsigned long long), h.stream));   // n_next, seed_next
+            ++h.launches;
+            k_dtt_stack<<<h.num_sms * 4, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
+            FMM_CHECK_LAUNCH("dtt stack");
+            FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
+            FMM_CUDA(cudaStreamSynchronize(h.stream));
+            if (hc->overflow) {
+                overflow = true;
+                break;
+            }
+            nfront = hc->n_next;
+            cur ^= 1;
+        }
+        if (!overflow) {
+            h.n_m2l = (int64_t)hc->n_m2l;
+            h.n_p2p = (int64_t)hc->n_p2p;
+            break;
+        }
+        if (attempt >= 2) {
+            set_error("dual tree traversal: list buffers overflowed after regrowing");
+            return FMM_ERR_CAPACITY;
+        }
+        // regrow what overflowed to what was counted (+25%) and run again
+        if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 5 / 4) + 1024);
+        if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 5 / 4) + 1024);
+        if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 4, (int64_t)(hc->n_next * 5 / 4) + 4096);
+    }
+    phase_end(h, FMM_PHASE_TRAVERSE);
+
+    phase_begin(h, FMM_PHASE_LISTS);
+    FMM_TRY(group_list(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off));
+    FMM_TRY(group_list(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off));
+    // P2P particle pairs (for the counters)
+    FMM_CUDA(cudaMemsetAsync(&ctr->p2p_pairs, 0, sizeof(unsigned long long), h.stream));
+    if (h.n_p2p > 0) {
+        ++h.launches;
+        k_p2p_pairs<<<std::min(ceil_div(h.n_p2p, 256), h.num_sms * 8), 256, 0, h.stream>>>(
+            h.p2p_raw.as<int2>(), h.n_p2p, h.c_pcnt.as<int>(), &ctr->p2p_pairs);
+    }
+    FMM_CHECK_LAUNCH("p2p pairs");
+    FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    h.p2p_pairs = (int64_t)hc->p2p_pairs;
+    h.nleaves = hc->nleaves;
+    phase_end(h, FMM_PHASE_LISTS);
+    return FMM_OK;
+}
+
+}  // namespace fmm

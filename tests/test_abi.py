@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads, and exports every entry point of include/fmm.h.
+
+No compute call is made here (no GPU on the build host); only argument checks
+that the library performs before touching the device are exercised.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fmm.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(fmm_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1209_3516_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("fmm_create", "fmm_build", "fmm_evaluate", "fmm_backward", "fmm_destroy",
+                     "fmm_last_error_string", "fmm_stats", "fmm_energy", "fmm_evaluate_host"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_argument_checks_before_any_device_call(lib):
+    lib.fmm_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int, ctypes.c_float,
+                               ctypes.c_int, ctypes.c_void_p]
+    lib.fmm_last_error_string.restype = ctypes.c_char_p
+    h = ctypes.c_void_p(1)
+    assert lib.fmm_create(ctypes.byref(h), 0, 4, 0.4, 64, None) == -1      # N < 1
+    assert h.value is None
+    assert b"N must be" in lib.fmm_last_error_string()
+    assert lib.fmm_create(ctypes.byref(h), 100, 4, 1.5, 64, None) == -1    # theta out of range
+    assert lib.fmm_create(ctypes.byref(h), 100, 4, float("nan"), 64, None) == -1
+    assert lib.fmm_create(ctypes.byref(h), 100, 4, 0.4, 0, None) == -1     # ncrit < 1
+    assert lib.fmm_create(ctypes.byref(h), 100, 7, 0.4, 64, None) == -2    # P not compiled
+    assert lib.fmm_create(None, 100, 4, 0.4, 64, None) == -1
+    assert lib.fmm_destroy(None) == 0
+    lib.fmm_build.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.fmm_build(None, None) == -1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1209_3516_gb300 import fmm
+    monkeypatch.setattr(fmm, "_lib", None)
+    monkeypatch.setattr(fmm._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        fmm.load()
+
+
+def test_product_path_does_not_touch_the_oracle():
+    # the package and its kernels never import, link, load or call the oracle
+    pkg = os.path.join(ROOT, "paper_1209_3516_gb300")
+    forbidden = re.compile(r"import\s+oracle|from\s+oracle|liborc|fmm_oracle|\borc_\w+\(")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not forbidden.search(text), f

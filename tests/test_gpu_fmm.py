@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (per the method's structure):
+  * Morton keys, sort permutation, normalisation, cells (ids, ranges, children,
+    parents, centres, FP32 radii) and both interaction lists: bit-exact
+    (lists compared as sorted sets of (target, source) cell pairs);
+  * potential and gradient: relative L2 error <= 1e-5 against the FP64 oracle
+    FMM at the same P, theta, ncrit (the FP32 path's tolerance); the error
+    against the FP64 direct sum is checked against the method's own accuracy.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1209_3516_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_1209_3516_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def run_gpu(torch, x, q, P, theta, ncrit, kahan=False):
+    from paper_1209_3516_gb300 import fmm
+    N = x.shape[0]
+    h = fmm.FMM(N, P, theta, ncrit, kahan=kahan)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    h.build(xd)
+    phi, grad = h.evaluate(qd)
+    torch.cuda.synchronize()
+    return h, phi.cpu().numpy(), grad.cpu().numpy()
+
+
+def pair_keys(pairs, ncells):
+    return np.sort(pairs[:, 0].astype(np.int64) * ncells + pairs[:, 1].astype(np.int64))
+
+
+def check_structure(h, ref):
+    keys, perm = h.sorted()
+    rs = ref.sorted()
+    assert np.array_equal(keys, rs["key"])
+    assert np.array_equal(perm.astype(np.int64), rs["perm"])
+    c, hh = h.norm()
+    rc, rh = ref.norm()
+    assert np.array_equal(c, rc) and hh == rh
+    g = h.cells()
+    r = ref.cells()
+    assert np.array_equal(g["canon"], r["canon"])
+    assert np.array_equal(g["level"], r["level"])
+    assert np.array_equal(g["pbeg"].astype(np.int64), r["pbeg"])
+    assert np.array_equal(g["pcnt"].astype(np.int64), r["pcnt"])
+    assert np.array_equal(g["nchild"], r["nchild"])
+    assert np.array_equal(g["parent"].astype(np.int64), r["parent"])
+    assert np.array_equal(g["centre"], r["centre"])
+    assert np.array_equal(g["radius"], r["radius"])
+    m, p = h.lists()
+    om, op = ref.lists_idx()
+    nc = len(r["canon"])
+    assert np.array_equal(pair_keys(m, nc), pair_keys(om, nc))
+    assert np.array_equal(pair_keys(p, nc), pair_keys(op, nc))
+    # the library's lists are grouped and sorted by (target, source)
+    km = m[:, 0].astype(np.int64) * nc + m[:, 1]
+    assert np.all(np.diff(km) > 0)
+
+
+CASES = [
+    # N, P, theta, ncrit, kind
+    (16384, 4, 0.4, 64, "u"),      # the small plain-FMM workload
+    (16384, 3, 0.5, 64, "u"),
+    (16384, 5, 0.3, 64, "u"),
+    (16384, 6, 0.4, 64, "u"),
+    (16384, 8, 0.4, 64, "u"),
+    (33333, 4, 0.45, 32, "u"),     # ragged sizes: several tiles, partial last tile
+    (5001, 4, 0.4, 17, "u"),
+    (20000, 4, 0.4, 32, "p"),      # adaptive (Plummer): deep, uneven tree
+    (9000, 6, 0.5, 8, "p"),
+]
+
+
+@pytest.mark.parametrize("N,P,theta,ncrit,kind", CASES)
+def test_parity_with_oracle(torch_cuda, N, P, theta, ncrit, kind):
+    x, q = inputs.uniform_cube(N, 1209 + N) if kind == "u" else inputs.plummer(N, 1211 + N)
+    if kind == "p":
+        q = inputs.rng(7 + N).random(N) * 2 - 1
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit)
+    ref = oracle.FMM(N, P, theta, ncrit).build(x)
+    check_structure(h, ref)
+    pr, gr = ref.evaluate(q32)
+    assert rel_l2(phi, pr) <= TOL, rel_l2(phi, pr)
+    assert rel_l2(grad, gr) <= TOL, rel_l2(grad, gr)
+    # energy: FP64 reduction of the FP32 potentials
+    E = h.energy()
+    Er = 0.5 * float(q32 @ pr)
+    assert abs(E - Er) <= 1e-5 * abs(Er) + 1e-7 * float(np.abs(q32) @ np.abs(pr))
+    h.close()
+
+
+def test_theta_zero_is_the_direct_sum(torch_cuda):
+    N = 12000
+    x, q = inputs.uniform_cube(N, 77)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, 4, 0.0, 64)
+    assert h.lists(fetch=False)[0] == 0
+    pd, gd = oracle.direct(x, q32)
+    assert rel_l2(phi, pd) <= TOL
+    assert rel_l2(grad, gd) <= TOL
+    h.close()
+
+
+def test_accuracy_against_direct_sum(torch_cuda):
+    # the FMM error (FP32 path) stays at the level of the FP64 oracle FMM
+    N = 16384
+    x, q = inputs.uniform_cube(N, 1209)
+    q32 = q.astype(np.float32).astype(np.float64)
+    pd, gd = oracle.direct(x, q32)
+    for P, theta in ((4, 0.4), (6, 0.4), (8, 0.3)):
+        h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, 64)
+        pr, gr = oracle.FMM(N, P, theta, 64).build(x).evaluate(q32)
+        e_gpu, e_orc = rel_l2(grad, gd), rel_l2(gr, gd)
+        assert e_gpu <= e_orc * 1.05 + 2 * TOL, (P, theta, e_gpu, e_orc)
+        h.close()
+
+
+@pytest.mark.parametrize("N,ncrit", [(1, 64), (2, 64), (3, 1), (64, 64), (65, 64), (100, 1), (4097, 4096)])
+def test_small_and_boundary_sizes(torch_cuda, N, ncrit):
+    x, q = inputs.uniform_cube(N, 300 + N)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, 4, 0.4, ncrit)
+    ref = oracle.FMM(N, 4, 0.4, ncrit).build(x)
+    check_structure(h, ref)
+    pr, gr = ref.evaluate(q32)
+    if N == 1:
+        assert phi[0] == 0.0 and np.all(grad == 0.0)
+    else:
+        assert rel_l2(phi, pr) <= TOL
+        assert rel_l2(grad, gr) <= TOL
+    h.close()
+
+
+def test_coincident_particles(torch_cuda):
+    # 200 copies of one point plus a few others: a chain of cells down to level 21,
+    # a level-21 leaf above ncrit, and r = 0 pairs contributing nothing
+    rng = inputs.rng(5)
+    x = np.concatenate([np.full((200, 3), 0.3), rng.random((57, 3))])
+    q = rng.random(257) - 0.5
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, 4, 0.4, 16)
+    ref = oracle.FMM(257, 4, 0.4, 16).build(x)
+    check_structure(h, ref)
+    assert h.cells()["level"].max() == 21
+    pr, gr = ref.evaluate(q32)
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(grad))
+    assert rel_l2(phi, pr) <= TOL
+    assert rel_l2(grad, gr) <= TOL
+    h.close()
+
+
+def test_repeated_evaluations_and_rebuild(torch_cuda):
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 8000
+    x, q = inputs.uniform_cube(N, 91)
+    x2, _ = inputs.uniform_cube(N, 92)
+    h = fmm.FMM(N, 4, 0.4, 32)
+    xd = torch.from_numpy(x).cuda()
+    ref = oracle.FMM(N, 4, 0.4, 32).build(x)
+    for k in range(3):
+        qk = (inputs.rng(100 + k).random(N) * 2 - 1).astype(np.float32)
+        phi, grad = h.evaluate(torch.from_numpy(qk).cuda(), x=xd)
+        pr, gr = ref.evaluate(qk.astype(np.float64))
+        assert rel_l2(phi.cpu().numpy(), pr) <= TOL
+        assert rel_l2(grad.cpu().numpy(), gr) <= TOL
+    # a different x pointer triggers a rebuild
+    x2d = torch.from_numpy(x2).cuda()
+    phi, grad = h.evaluate(torch.from_numpy(q.astype(np.float32)).cuda(), x=x2d)
+    pr, gr = oracle.FMM(N, 4, 0.4, 32).build(x2).evaluate(q.astype(np.float32).astype(np.float64))
+    assert rel_l2(phi.cpu().numpy(), pr) <= TOL
+    h.close()
+
+
+def test_host_buffer_path_matches_device_path(torch_cuda):
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 10000
+    x, q = inputs.uniform_cube(N, 93)
+    q32 = q.astype(np.float32)
+    h = fmm.FMM(N, 4, 0.4, 64)
+    ph, gh = h.evaluate_host(x, q32)
+    pd, gd = h.evaluate(torch.from_numpy(q32).cuda(), x=torch.from_numpy(x).cuda())
+    assert np.array_equal(ph, pd.cpu().numpy())
+    assert np.array_equal(gh, gd.cpu().numpy())
+    h.close()
+
+
+def test_errors_are_reported(torch_cuda):
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 1000
+    x, q = inputs.uniform_cube(N, 94)
+    x[17, 1] = np.nan
+    h = fmm.FMM(N, 4, 0.4, 64)
+    with pytest.raises(fmm.FMMError) as e:
+        h.build(torch.from_numpy(x).cuda())
+    assert e.value.code == fmm.FMM_ERR_INPUT
+    with pytest.raises(fmm.FMMError) as e:
+        h.evaluate(torch.zeros(N, dtype=torch.float32, device="cuda"))
+    assert e.value.code == fmm.FMM_ERR_STATE
+    h.close()
+    with pytest.raises(fmm.FMMError) as e:
+        fmm.FMM(N, 7, 0.4, 64)
+    assert e.value.code == fmm.FMM_ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_full_size_uniform_1m(torch_cuda):
+    # the N = 1,048,576 workload of the benchmark, P = 4, theta = 0.4, ncrit = 64:
+    # tree and lists bit-exact; potential/gradient on a 4,096-target sample
+    N, P, theta, ncrit = 1048576, 4, 0.4, 64
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit)
+    ref = oracle.FMM(N, P, theta, ncrit).build(x)
+    check_structure(h, ref)
+    t = inputs.sample_targets(N, 4096)
+    pr, gr = ref.evaluate(q32, t)
+    assert rel_l2(phi[t], pr) <= TOL
+    assert rel_l2(grad[t], gr) <= TOL
+    pd, gd = oracle.direct(x, q32, t)
+    st = h.stats()
+    print("N=1M P=4 theta=0.4: err vs direct phi %.2e grad %.2e; cells %d M2L %d P2P %d pairs %d"
+          % (rel_l2(phi[t], pd), rel_l2(grad[t], gd), st["ncells"], st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
+    h.close()
