@@ -99,7 +99,7 @@ static int do_build(Handle &h, const double *x)
     const int ev0 = 2 * kPhases, ev1 = 2 * kPhases + 1;
     if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
     FMM_TRY(build_keys(h, x));
-    FMM_TRY(build_tree(h));
+    FMM_TRY(build_tree(h, x));
     FMM_TRY(build_lists(h));
     FMM_TRY(build_p2p_items(h));
     if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);

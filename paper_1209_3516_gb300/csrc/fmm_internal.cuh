@@ -1,9 +1,10 @@
 // fmm_internal.cuh -- internal declarations of the GB300 DTT-FMM library.
 //
 // Data layout in HBM (all owned by the handle):
-//   particles  : float4 pos[N] in Morton order, (u_x, u_y, u_z, q) with u the
-//                position normalised to (-1,1)^3, rounded to FP32; perm[N] int32
-//                maps sorted slot -> caller index.
+//   particles  : float4 pos[N] in Morton order, (d_x, d_y, d_z, q) with d = u - X_leaf
+//                the offset of the normalised position u in (-1,1)^3 from the centre
+//                of the particle's leaf, rounded once to FP32; perm[N] int32 maps
+//                sorted slot -> caller index.
 //   cells      : breadth-first order (level by level, Morton order inside a
 //                level).  Structure-of-arrays: prefix (u64), level, pbeg,
 //                pcnt, cbeg, ccnt, parent (int32), geom float4 (centre, radius).
@@ -134,7 +135,7 @@ struct Handle {
     DevBuf p2p_src, p2p_off;
     DevBuf leaf_list;          // int32 leaf cell ids
     DevBuf p2p_items;          // int4 (leaf, first target, target count, 0) work items of the P2P kernel
-    DevBuf p2p_rng;            // int2 (first particle, count) per P2P list entry
+    DevBuf p2p_rng;            // int4 (first particle, count, source leaf, 0) per P2P list entry
     int64_t n_items = 0;
     DevBuf pairs_count;        // u64 scratch (P2P particle-pair count)
 
@@ -166,7 +167,7 @@ int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, 
                     int end_bit);
 
 int build_keys(Handle &h, const double *x);       // bbox, normalise, Morton, sort, gather
-int build_tree(Handle &h);                        // cells, geometry
+int build_tree(Handle &h, const double *x);       // cells, geometry, leaf-local positions
 int build_lists(Handle &h);                       // DTT + grouping
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
 

@@ -10,6 +10,9 @@
 //     concatenated sequence (float4 (x, y, z, q) loads, coalesced inside each
 //     leaf), each lane computing 16 pair interactions per source with one SFU
 //     rsqrt each;
+//   - positions are FP32 offsets from the leaf centre; a source is moved into
+//     the target leaf's frame by the exact (dyadic) shift X_S - X_T, so close
+//     pairs keep ~2^-24 of the leaf size in absolute precision;
 //   - the 4 x 16 accumulators are reduce-scattered across the warp (62
 //     shuffles), then lanes 2g / 2g+1 own target g: L2P of the leaf's local
 //     expansion is added, units restored (phi / h, grad / h^2) and the result
@@ -52,13 +55,13 @@ __global__ void k_p2p_item_write(int nleaves, const int *leaf_list, const int *p
     }
 }
 
-// Source ranges (first particle, count) of every P2P list entry.
-__global__ void k_p2p_ranges(int64_t n, const int *src, const int *pbeg, const int *pcnt, int2 *rng)
+// Source ranges (first particle, count, source leaf) of every P2P list entry.
+__global__ void k_p2p_ranges(int64_t n, const int *src, const int *pbeg, const int *pcnt, int4 *rng)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int s = src[e];
-    rng[e] = make_int2(pbeg[s], pcnt[s]);
+    rng[e] = make_int4(pbeg[s], pcnt[s], s, 0);
 }
 
 // Reduce-scatter 2 * NV values across the warp by recursive halving.
@@ -81,7 +84,7 @@ __device__ __forceinline__ void warp_reduce_scatter64(float *v)
 }
 
 template <int P, bool kKahan>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *items, const int *off, const int2 *rng,
+__global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *items, const int *off, const int4 *rng,
                                                      const float4 *pos, const float4 *geom, const int *level,
                                                      const float *L, const int *perm, float phi_scale,
                                                      float grad_scale, float *phi, float *grad, float *phi_sorted)
@@ -94,6 +97,9 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
     const int4 it = items[item];
     const int leaf = it.x, tb = it.y, tc = it.z;
 
+    // targets and sources are offsets from their leaf centres; a source of leaf S
+    // is moved into the target leaf's frame by the exact shift X_S - X_T
+    const float4 Xt = geom[leaf];
     float tx[G], ty[G], tz[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -113,18 +119,39 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
         for (int i = 0; i < 4 * G; ++i) comp[i] = blk[i] = 0.0f;
     }
 
+    // per-lane cursor over the concatenated source particles of the item's list:
+    // entry e, offset o inside it, its range r and its frame shift
     const int e1 = off[leaf + 1];
     int e = off[leaf];
     int o = (int)lane;
-    int2 r = e < e1 ? rng[e] : make_int2(0, 0);
-    while (e < e1 && o >= r.y) {
-        o -= r.y;
-        ++e;
-        r = e < e1 ? rng[e] : make_int2(0, 0);
+    int4 r = make_int4(0, 0, 0, 0);
+    float shx = 0.f, shy = 0.f, shz = 0.f;
+    bool fresh = true;
+    for (;;) {
+        if (fresh) r = e < e1 ? rng[e] : make_int4(0, 0, 0, 0);
+        if (e < e1 && o >= r.y) {
+            o -= r.y;
+            ++e;
+            fresh = true;
+            continue;
+        }
+        break;
+    }
+    if (e < e1) {
+        const float4 Xs = geom[r.z];
+        shx = Xs.x - Xt.x;
+        shy = Xs.y - Xt.y;
+        shz = Xs.z - Xt.z;
     }
     int nsub = 0;
     while (__any_sync(kFull, e < e1)) {
-        const float4 s = e < e1 ? pos[r.x + o] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < e1) {
+            s = pos[r.x + o];
+            s.x += shx;
+            s.y += shy;
+            s.z += shz;
+        }
 #pragma unroll
         for (int sb = 0; sb < G / 4; ++sb) {
             if (4 * sb < tc) {
@@ -157,10 +184,18 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
             }
         }
         o += 32;
-        while (e < e1 && o >= r.y) {
-            o -= r.y;
-            ++e;
-            r = e < e1 ? rng[e] : make_int2(0, 0);
+        if (e < e1 && o >= r.y) {
+            do {
+                o -= r.y;
+                ++e;
+                r = e < e1 ? rng[e] : make_int4(0, 0, 0, 0);
+            } while (e < e1 && o >= r.y);
+            if (e < e1) {
+                const float4 Xs = geom[r.z];
+                shx = Xs.x - Xt.x;
+                shy = Xs.y - Xt.y;
+                shz = Xs.z - Xt.z;
+            }
         }
     }
     if (kKahan) {
@@ -181,12 +216,11 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
     const float4 p = pos[sidx];
     float pot = v[0], gx = v[1], gy = o0, gz = o1;
 
-    // L2P: phi += sum_n Lb_n w_n(r / s), grad += (1/s) sum_m Lb_{m + e_d} w_m(r / s)
+    // L2P: phi += sum_n Lb_n w_n(r / s), grad += (1/s) sum_m Lb_{m + e_d} w_m(r / s), r = p (leaf offset)
     {
-        const float4 X = geom[leaf];
         const float inv_s = ldexpf(1.0f, level[leaf]);
         float w[T];
-        taylor_monomials<P>((p.x - X.x) * inv_s, (p.y - X.y) * inv_s, (p.z - X.z) * inv_s, w);
+        taylor_monomials<P>(p.x * inv_s, p.y * inv_s, p.z * inv_s, w);
         const float *Lc = L + (size_t)leaf * TP;
         float lp = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
 #pragma unroll
@@ -235,11 +269,11 @@ int build_p2p_items(Handle &h)
     ++h.launches;
     k_p2p_item_write<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
                                                               h.c_pcnt.as<int>(), off, h.p2p_items.as<int4>());
-    FMM_TRY(h.p2p_rng.reserve(std::max<int64_t>(h.n_p2p, 1) * sizeof(int2)));
+    FMM_TRY(h.p2p_rng.reserve(std::max<int64_t>(h.n_p2p, 1) * sizeof(int4)));
     if (h.n_p2p > 0) {
         ++h.launches;
         k_p2p_ranges<<<ceil_div(h.n_p2p, 256), 256, 0, h.stream>>>(h.n_p2p, h.p2p_src.as<int>(), h.c_pbeg.as<int>(),
-                                                                 h.c_pcnt.as<int>(), h.p2p_rng.as<int2>());
+                                                                 h.c_pcnt.as<int>(), h.p2p_rng.as<int4>());
     }
     FMM_CHECK_LAUNCH("p2p items");
     return FMM_OK;
@@ -253,13 +287,13 @@ template <int P> static int p2p_impl(Handle &h, float *phi, float *grad)
     if (h.flags & FMM_FLAG_KAHAN) {
         ++h.launches;
         k_p2p<P, true><<<blocks, kP2PThreads, 0, h.stream>>>(
-            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int2>(), h.pos.as<float4>(),
+            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int4>(), h.pos.as<float4>(),
             h.c_geom.as<float4>(), h.c_level.as<int>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
             grad, h.phi_sorted.as<float>());
     } else {
         ++h.launches;
         k_p2p<P, false><<<blocks, kP2PThreads, 0, h.stream>>>(
-            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int2>(), h.pos.as<float4>(),
+            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int4>(), h.pos.as<float4>(),
             h.c_geom.as<float4>(), h.c_level.as<int>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
             grad, h.phi_sorted.as<float>());
     }

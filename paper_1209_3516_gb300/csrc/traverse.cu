@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 
 #include "device_util.cuh"
 #include "fmm_internal.cuh"
@@ -343,14 +344,20 @@ int build_lists(Handle &h)
             h.n_p2p = (int64_t)hc->n_p2p;
             break;
         }
-        if (attempt >= 2) {
-            set_error("dual tree traversal: list buffers overflowed after regrowing");
+        if (attempt >= 12) {
+            char msg[256];
+            snprintf(msg, sizeof(msg),
+                     "dual tree traversal: buffers still overflow after %d regrowths (flags %u, caps m2l %lld "
+                     "p2p %lld frontier %lld)",
+                     attempt, hc->overflow, (long long)h.m2l_cap, (long long)h.p2p_cap, (long long)h.front_cap);
+            set_error(msg);
             return FMM_ERR_CAPACITY;
         }
-        // regrow what overflowed to what was counted (+25%) and run again
-        if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 5 / 4) + 1024);
-        if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 5 / 4) + 1024);
-        if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 4, (int64_t)(hc->n_next * 5 / 4) + 4096);
+        // The traversal stopped at the first overflow, so the counters are lower
+        // bounds: at least double what overflowed and run again.
+        if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 3 / 2) + 1024);
+        if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 3 / 2) + 1024);
+        if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 2, (int64_t)(hc->n_next * 3 / 2) + 4096);
     }
     phase_end(h, FMM_PHASE_TRAVERSE);
 

@@ -372,6 +372,25 @@ __global__ void k_radius_final(int nc, const unsigned *r2bits, float4 *geom)
     geom[c].w = __fsqrt_rn(__uint_as_float(r2bits[c]));
 }
 
+// Particle positions stored as FP32 offsets from the centre of their leaf,
+// d = u - X_leaf, rounded once from FP64 (u recomputed exactly as for the keys).
+// Leaf centres are exact in FP32, so the kernels recover differences of nearby
+// particles to ~2^-24 of the leaf size instead of 2^-24 of the domain size.
+__global__ void k_local_positions(const double *x, int64_t n, const int *perm, const double *norm, const int *leaf_of,
+                                  const float4 *geom, float4 *pos)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    const double h = norm[3];
+    const float4 X = geom[leaf_of[s]];
+    const double cx = X.x, cy = X.y, cz = X.z;
+    const double ux = __ddiv_rn(__dsub_rn(x[3 * i + 0], norm[0]), h);
+    const double uy = __ddiv_rn(__dsub_rn(x[3 * i + 1], norm[1]), h);
+    const double uz = __ddiv_rn(__dsub_rn(x[3 * i + 2], norm[2]), h);
+    pos[s] = make_float4(__double2float_rn(ux - cx), __double2float_rn(uy - cy), __double2float_rn(uz - cz), 0.0f);
+}
+
 static int grow_cells(Handle &h, int64_t need)
 {
     if (need <= h.cell_cap) return FMM_OK;
@@ -387,7 +406,7 @@ static int grow_cells(Handle &h, int64_t need)
     return FMM_OK;
 }
 
-int build_tree(Handle &h)
+int build_tree(Handle &h, const double *x)
 {
     const int64_t N = h.N;
     phase_begin(h, FMM_PHASE_TREE);
@@ -452,6 +471,11 @@ int build_tree(Handle &h)
         h.c_r2bits.as<unsigned>());
     ++h.launches;
     k_radius_final<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_r2bits.as<unsigned>(), h.c_geom.as<float4>());
+    // from here on particles are stored relative to their leaf centre
+    ++h.launches;
+    k_local_positions<<<ceil_div(N, 256), 256, 0, h.stream>>>(x, N, h.perm.as<int>(), h.norm.as<double>(),
+                                                              h.leaf_of.as<int>(), h.c_geom.as<float4>(),
+                                                              h.pos.as<float4>());
     FMM_CHECK_LAUNCH("geometry");
     phase_end(h, FMM_PHASE_TREE);
     return FMM_OK;
