@@ -155,6 +155,27 @@ int fmm_energy(fmm_handle *h, double *E);
  */
 int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq, float *dx);
 
+/*
+ * fmm_energy_noalloc -- E = 1/2 sum_i q_i phi_i of caller arrays, reduced in FP64,
+ * WITHOUT allocating any memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc, such as
+ * applications that hand out all device memory from their own arena or a
+ * framework's caching allocator and budget it up front.
+ *   q, phi  device arrays of n FP32 values (any particle order, the same in both).
+ *   n       1 <= n <= 16,777,216; larger n returns FMM_ERR_ARG.  The limit comes
+ *           from the scratch: one FP64 partial per 2048 values in a fixed 64 KiB
+ *           array of the library's device memory, which every GPU that loads the
+ *           library holds until the process exits.
+ *   E       out, DEVICE pointer to one double.
+ *   stream  cudaStream_t to run on (NULL = legacy default stream); asynchronous.
+ * The first call on a device (with that device current) looks up the scratch
+ * array's device address; make that first call before any stream capture.  All
+ * calls share the scratch array, so calls that overlap on the GPU (different
+ * streams or threads) race; the array keeps the last call's contents, and each
+ * call writes every partial it reads.
+ */
+int fmm_energy_noalloc(const float *q, const float *phi, int64_t n, double *E, void *stream);
+
 /* fmm_stats -- counters and timings of the last build/evaluate into *s (HOST). */
 int fmm_stats(fmm_handle *h, struct fmm_stats *s);
 

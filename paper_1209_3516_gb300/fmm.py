@@ -78,6 +78,7 @@ def load():
     L.fmm_get_ncells.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.fmm_get_cells.argtypes = [_vp] + [_vp] * 8
     L.fmm_get_lists.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _vp, _vp]
+    L.fmm_energy_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
     _lib = L
     return L
 
@@ -100,6 +101,19 @@ def _dev_ptr(t, dtype, shape, name):
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError("%s must be contiguous with shape %s, got %s" % (name, shape, tuple(t.shape)))
     return t.data_ptr()
+
+
+def energy_noalloc(q, phi, E, stream=None):
+    """fmm_energy_noalloc: E[0] = 1/2 sum q phi into the caller's device double E (no allocation)."""
+    import torch
+    n = q.numel()
+    qp = _dev_ptr(q, torch.float32, (n,), "q")
+    pp = _dev_ptr(phi, torch.float32, (n,), "phi")
+    ep = _dev_ptr(E, torch.float64, (1,), "E")
+    if stream is None:
+        stream = torch.cuda.current_stream(q.device)
+    _check(load().fmm_energy_noalloc(qp, pp, n, ep, ctypes.c_void_p(stream.cuda_stream)))
+    return E
 
 
 class FMM:
