@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-                     "-I" + os.path.join(ROOT, "include")]
+                     "-I" + os.path.join(ROOT, "include")] + os.environ.get("FMM_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:

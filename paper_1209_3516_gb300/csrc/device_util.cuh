@@ -17,6 +17,15 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Hardware reciprocal square root (SFU, ~2^-23 relative error), denormal inputs
+// flushed to zero.  Callers pass normal positive numbers (or 0, giving +inf).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <class T> __device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll

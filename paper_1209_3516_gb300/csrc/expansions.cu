@@ -45,21 +45,26 @@ template <int T, int TP> __device__ __forceinline__ void warp_store_vec(const fl
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const int *pcnt, const int *level,
-                      const float4 *pos, float *M)
+                      const int *parent, const float4 *geom, const float4 *pos, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= nleaves) return;
     const int c = leaf_list[warp];
     const float inv_s = ldexpf(1.0f, level[c]);
+    // particles are offsets d from the frame centre X_F (the leaf's parent):
+    // (X_C - u) / s = (X_C - X_F) / s - d / s, the first term exactly 0 or +-1
+    const int fr = parent[c] >= 0 ? parent[c] : c;
+    const float4 Xc = geom[c], Xf = geom[fr];
+    const float ox = (Xc.x - Xf.x) * inv_s, oy = (Xc.y - Xf.y) * inv_s, oz = (Xc.z - Xf.z) * inv_s;
     float acc[T];
 #pragma unroll
     for (int i = 0; i < T; ++i) acc[i] = 0.0f;
     const int b = pbeg[c], e = b + pcnt[c];
     for (int j = b + (int)lane_id(); j < e; j += 32) {
-        const float4 p = pos[j];   // offset from the leaf centre X
+        const float4 p = pos[j];
         float w[T];
-        taylor_monomials<P>(-p.x * inv_s, -p.y * inv_s, -p.z * inv_s, w);
+        taylor_monomials<P>(fmaf(-p.x, inv_s, ox), fmaf(-p.y, inv_s, oy), fmaf(-p.z, inv_s, oz), w);
 #pragma unroll
         for (int i = 0; i < T; ++i) acc[i] = fmaf(p.w, w[i], acc[i]);
     }
@@ -228,6 +233,7 @@ template <int P> static int upward_impl(Handle &h, const float *q)
     ++h.launches;
     k_p2m<P><<<ceil_div((int64_t)nl * 32, 128), 128, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
                                                                     h.c_pcnt.as<int>(), h.c_level.as<int>(),
+                                                                    h.c_parent.as<int>(), h.c_geom.as<float4>(),
                                                                     h.pos.as<float4>(), h.M.as<float>());
     for (int l = h.nlevels - 2; l >= 0; --l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);

@@ -1,10 +1,10 @@
 // fmm_internal.cuh -- internal declarations of the GB300 DTT-FMM library.
 //
 // Data layout in HBM (all owned by the handle):
-//   particles  : float4 pos[N] in Morton order, (d_x, d_y, d_z, q) with d = u - X_leaf
+//   particles  : float4 pos[N] in Morton order, (d_x, d_y, d_z, q) with d = u - X_frame
 //                the offset of the normalised position u in (-1,1)^3 from the centre
-//                of the particle's leaf, rounded once to FP32; perm[N] int32 maps
-//                sorted slot -> caller index.
+//                of the parent of the particle's leaf, rounded once to FP32; perm[N]
+//                int32 maps sorted slot -> caller index.
 //   cells      : breadth-first order (level by level, Morton order inside a
 //                level).  Structure-of-arrays: prefix (u64), level, pbeg,
 //                pcnt, cbeg, ccnt, parent (int32), geom float4 (centre, radius).
@@ -134,8 +134,11 @@ struct Handle {
     DevBuf m2l_src, m2l_off;   // int32 sources, CSR offsets (ncells + 1)
     DevBuf p2p_src, p2p_off;
     DevBuf leaf_list;          // int32 leaf cell ids
-    DevBuf p2p_items;          // int4 (leaf, first target, target count, 0) work items of the P2P kernel
-    DevBuf p2p_rng;            // int4 (first particle, count, source leaf, 0) per P2P list entry
+    DevBuf p2p_items;          // int4 (leaf, first target, target count, leaf-list index) P2P work items
+    DevBuf p2p_poff;           // u32 first source run of each leaf (leaf-list order), nleaves + 1
+    DevBuf p2p_ent;            // float4 (X_frame(S) - X_frame(T), first particle) per source run
+    DevBuf p2p_cnt;            // int end particle (exclusive) per source run
+    int64_t n_pieces = 0;      // source runs over all target leaves
     int64_t n_items = 0;
     DevBuf pairs_count;        // u64 scratch (P2P particle-pair count)
 

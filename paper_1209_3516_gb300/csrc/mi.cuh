@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include "device_util.cuh"
+
 namespace fmm {
 
 template <int P> struct MI {
@@ -62,7 +64,7 @@ template <int P>
 __device__ __forceinline__ void laplace_derivatives(float Rx, float Ry, float Rz, float *D)
 {
     const float r2 = fmaf(Rz, Rz, fmaf(Ry, Ry, Rx * Rx));
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_approx(r2);   // |R| >= 1 cell half-width: normal, positive
     const float rinv2 = rinv * rinv;
     D[0] = rinv;
 #pragma unroll

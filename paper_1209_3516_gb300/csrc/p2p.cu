@@ -5,14 +5,18 @@
 // (pairs at distance 0 contribute nothing).  The paper's kernel is AVX with
 // rsqrt_ps (Sec. 3.3); here:
 //   - work item = (target leaf, slice of <= 16 of its targets); one warp per item;
-//   - the 16 target positions sit in registers (warp-uniform), the warp's 32
-//     lanes stream the source particles of all listed leaves as one
-//     concatenated sequence (float4 (x, y, z, q) loads, coalesced inside each
-//     leaf), each lane computing 16 pair interactions per source with one SFU
-//     rsqrt each;
-//   - positions are FP32 offsets from the leaf centre; a source is moved into
-//     the target leaf's frame by the exact (dyadic) shift X_S - X_T, so close
-//     pairs keep ~2^-24 of the leaf size in absolute precision;
+//   - the 16 target positions sit in registers (warp-uniform); the listed
+//     source leaves are merged into runs of consecutive siblings (one
+//     contiguous block of particles in one frame), and the runs are staged
+//     per warp in shared memory, 256 particles per chunk, double-buffered
+//     with cp.async so the next chunk streams in while the current one is
+//     used; each lane takes one staged source per step and computes its 16
+//     pair interactions, two targets per packed FP32 instruction (FFMA2,
+//     FADD2, FMUL2) and one SFU rsqrt per pair;
+//   - positions are FP32 offsets from the centre of the leaf's parent (the
+//     frame); a source is moved into the target's frame by the exact (dyadic)
+//     shift X_frame(S) - X_frame(T), so close pairs keep ~2^-24 of the frame
+//     size in absolute precision;
 //   - the 4 x 16 accumulators are reduce-scattered across the warp (62
 //     shuffles), then lanes 2g / 2g+1 own target g: L2P of the leaf's local
 //     expansion is added, units restored (phi / h, grad / h^2) and the result
@@ -32,7 +36,19 @@ namespace fmm {
 constexpr int kP2PG = 16;          // targets per work item
 constexpr int kP2PThreads = 128;
 
-// Work items: one per slice of <= 16 targets of a leaf, slices balanced in size.
+#ifndef FMM_P2P_SLOTS
+#define FMM_P2P_SLOTS 256
+#endif
+#ifndef FMM_P2P_MIN_BLOCKS
+#define FMM_P2P_MIN_BLOCKS 3
+#endif
+constexpr int kSlots = FMM_P2P_SLOTS;   // staged source particles per buffer
+constexpr int kP2PSmem = (kP2PThreads / 32) * 4 * kSlots * (int)sizeof(float4);   // 2 buffers x (particles + shifts)
+
+__device__ __forceinline__ int frame_of(const int *parent, int c) { return parent[c] >= 0 ? parent[c] : c; }
+
+// Work items: one per slice of <= 16 targets of a leaf, slices balanced in size;
+// item = (leaf cell, first target, target count, index of the leaf in the leaf list).
 __global__ void k_p2p_item_count(int nleaves, const int *leaf_list, const int *pcnt, unsigned *cnt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,21 +67,69 @@ __global__ void k_p2p_item_write(int nleaves, const int *leaf_list, const int *p
     const int ns = (nt + kP2PG - 1) / kP2PG;
     for (int k = 0; k < ns; ++k) {
         const int t0 = (int)((int64_t)nt * k / ns), t1 = (int)((int64_t)nt * (k + 1) / ns);
-        items[off[i] + k] = make_int4(c, b + t0, t1 - t0, 0);
+        items[off[i] + k] = make_int4(c, b + t0, t1 - t0, i);
     }
 }
 
-// Source ranges (first particle, count, source leaf) of every P2P list entry.
-__global__ void k_p2p_ranges(int64_t n, const int *src, const int *pbeg, const int *pcnt, int4 *rng)
+// Source runs: maximal stretches of consecutive list entries whose leaves share
+// a frame cell and follow each other in particle order (runs of siblings), so
+// that a run is one contiguous block of particles in one frame.
+__device__ __forceinline__ bool run_continues(int a, int b, const int *parent, const int *pbeg, const int *pcnt)
 {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const int s = src[e];
-    rng[e] = make_int4(pbeg[s], pcnt[s], s, 0);
+    return frame_of(parent, a) == frame_of(parent, b) && pbeg[a] + pcnt[a] == pbeg[b];
 }
 
-// Reduce-scatter 2 * NV values across the warp by recursive halving.
-// On return lane l holds entries 2l and 2l+1 of the warp-wide sums (NV = 32).
+__global__ void k_p2p_run_count(int nleaves, const int *leaf_list, const int *off, const int *src, const int *parent,
+                                const int *pbeg, const int *pcnt, unsigned *nruns)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaves) return;
+    const int t = leaf_list[w];
+    const int eb = off[t], ee = off[t + 1];
+    unsigned n = 0;
+    for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + (int)lane_id();
+        bool start = false;
+        if (e < ee) start = e == eb || !run_continues(src[e - 1], src[e], parent, pbeg, pcnt);
+        n += __popc(__ballot_sync(kFull, start));
+    }
+    if (lane_id() == 0) nruns[w] = n;
+}
+
+// Run records: (X_frame(S) - X_frame(T), first particle) and the end particle.
+__global__ void k_p2p_runs(int nleaves, const int *leaf_list, const int *off, const int *src, const int *parent,
+                           const int *pbeg, const int *pcnt, const float4 *geom, const unsigned *roff, float4 *run,
+                           int *run_end)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaves) return;
+    const unsigned lane = lane_id();
+    const int t = leaf_list[w];
+    const float4 Xt = geom[frame_of(parent, t)];
+    const int eb = off[t], ee = off[t + 1];
+    unsigned before = roff[w];
+    for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + (int)lane;
+        bool start = false, last = false;
+        int s = 0;
+        if (e < ee) {
+            s = src[e];
+            start = e == eb || !run_continues(src[e - 1], s, parent, pbeg, pcnt);
+            last = e + 1 == ee || !run_continues(s, src[e + 1], parent, pbeg, pcnt);
+        }
+        const unsigned m = __ballot_sync(kFull, start);
+        const unsigned r = before + __popc(m & (lanemask_lt() | (1u << lane))) - 1u;
+        if (start) {
+            const float4 Xs = geom[frame_of(parent, s)];
+            run[r] = make_float4(Xs.x - Xt.x, Xs.y - Xt.y, Xs.z - Xt.z, __int_as_float(pbeg[s]));
+        }
+        if (last) run_end[r] = pbeg[s] + pcnt[s];
+        before += __popc(m);
+    }
+}
+
+// Reduce-scatter 64 values across the warp by recursive halving: on return
+// lane l holds entries 2l and 2l+1 of the warp-wide sums.
 __device__ __forceinline__ void warp_reduce_scatter64(float *v)
 {
     const unsigned lane = lane_id();
@@ -83,128 +147,211 @@ __device__ __forceinline__ void warp_reduce_scatter64(float *v)
     }
 }
 
+// Accumulate the interactions of one source s (already in the target frame) with
+// NT targets, two targets per packed FP32 instruction (FFMA2 / FADD2 / FMUL2):
+// targets are held negated as float2 pairs (ntx[h] = -(t_2h, t_2h+1)), and
+// acc[4h + k] is component k (potential, gradient x, y, z) of that pair.
+// kExact: pairs at distance 0 contribute exactly nothing (needed where a
+// particle meets itself, in chunks holding the target leaf's own particles);
+// otherwise r^2 is clamped to FLT_MIN, which only matters for two distinct
+// particles that round to the same FP32 point and costs one instruction
+// instead of two.
+template <int NT, bool kExact>
+__device__ __forceinline__ void p2p_tile(const float4 &s, const float2 *ntx, const float2 *nty, const float2 *ntz,
+                                         float2 *acc)
+{
+    const float2 sx = make_float2(s.x, s.x), sy = make_float2(s.y, s.y), sz = make_float2(s.z, s.z);
+    const float2 sq = make_float2(s.w, s.w);
+#pragma unroll
+    for (int h = 0; h < NT / 2; ++h) {
+        const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        float2 rinv;
+        if (kExact) {
+            rinv.x = r2.x > 0.0f ? rsqrt_approx(r2.x) : 0.0f;
+            rinv.y = r2.y > 0.0f ? rsqrt_approx(r2.y) : 0.0f;
+        } else {
+            rinv.x = rsqrt_approx(fmaxf(r2.x, 1.17549435e-38f));
+            rinv.y = rsqrt_approx(fmaxf(r2.y, 1.17549435e-38f));
+        }
+        const float2 qr = __fmul2_rn(sq, rinv);
+        const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(rinv, rinv));
+        acc[4 * h + 0] = __fadd2_rn(acc[4 * h + 0], qr);
+        acc[4 * h + 1] = __ffma2_rn(qr3, dx, acc[4 * h + 1]);
+        acc[4 * h + 2] = __ffma2_rn(qr3, dy, acc[4 * h + 2]);
+        acc[4 * h + 3] = __ffma2_rn(qr3, dz, acc[4 * h + 3]);
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Warp-uniform cursor over an item's source runs, filling staging buffers.
+struct RunCursor {
+    int e, e1, o, pb, cnt;
+    float shx, shy, shz;
+    __device__ __forceinline__ void load(const float4 *run, const int *run_end)
+    {
+        if (e < e1) {
+            const float4 r = run[e];
+            shx = r.x;
+            shy = r.y;
+            shz = r.z;
+            pb = __float_as_int(r.w);
+            cnt = run_end[e] - pb;
+        }
+    }
+    // Copy up to kSlots particles into part (cp.async) with their frame shift in
+    // shift; *self is set when the copied particles overlap [tb0, tb1).
+    __device__ __forceinline__ int stage(const float4 *run, const int *run_end, const float4 *pos, float4 *part,
+                                         float4 *shift, int tb0, int tb1, bool *self)
+    {
+        const int lane = (int)lane_id();
+        int slots = 0;
+        bool sf = false;
+        while (slots < kSlots && e < e1) {
+            const int m = min(cnt - o, kSlots - slots);
+            const int begin = pb + o;
+            sf |= begin < tb1 && begin + m > tb0;
+            const float4 sh = make_float4(shx, shy, shz, 0.0f);
+            for (int i = lane; i < m; i += 32) {
+                cp_async16(part + slots + i, pos + begin + i);
+                shift[slots + i] = sh;
+            }
+            slots += m;
+            o += m;
+            if (o == cnt) {
+                ++e;
+                o = 0;
+                load(run, run_end);
+            }
+        }
+        *self = sf;
+        return slots;
+    }
+};
+
+// The source stream of one work item: double-buffered staging (the next chunk is
+// copied while the current one is used) and NT targets per staged source.
+// With kKahan the per-chunk partial sums (blk) are added to v with Kahan
+// compensation (comp) once per chunk.
+template <int NT, bool kKahan>
+__device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
+                                           float4 *buf, int lb0, int lb1, const float2 *ntx, const float2 *nty,
+                                           const float2 *ntz, float2 *v, float2 *comp, float2 *blk)
+{
+    const int lane = (int)lane_id();
+    bool self_cur = false, self_next = false;
+    int n_cur = cur.stage(run, run_end, pos, buf, buf + kSlots, lb0, lb1, &self_cur);
+    cp_async_commit();
+    for (int c = 0; n_cur > 0; ++c) {
+        float4 *cur_part = buf + (c & 1) * (2 * kSlots);
+        float4 *cur_shift = cur_part + kSlots;
+        float4 *nx = buf + ((c + 1) & 1) * (2 * kSlots);
+        const int n_next = cur.stage(run, run_end, pos, nx, nx + kSlots, lb0, lb1, &self_next);
+        cp_async_commit();
+        cp_async_wait_1();
+        __syncwarp();
+        float2 *acc = kKahan ? blk : v;
+        for (int t0 = 0; t0 < n_cur; t0 += 32) {
+            const int j = t0 + lane;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < n_cur) {
+                s = cur_part[j];
+                const float4 d = cur_shift[j];
+                s.x += d.x;
+                s.y += d.y;
+                s.z += d.z;
+            }
+            if (self_cur) p2p_tile<NT, true>(s, ntx, nty, ntz, acc);
+            else p2p_tile<NT, false>(s, ntx, nty, ntz, acc);
+        }
+        if (kKahan) {
+#pragma unroll
+            for (int i = 0; i < 2 * NT; ++i) {
+                const float2 y = make_float2(blk[i].x - comp[i].x, blk[i].y - comp[i].y);
+                const float2 t = make_float2(v[i].x + y.x, v[i].y + y.y);
+                comp[i] = make_float2((t.x - v[i].x) - y.x, (t.y - v[i].y) - y.y);
+                v[i] = t;
+                blk[i] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncwarp();   // every lane is done with this buffer before it is refilled
+        n_cur = n_next;
+        self_cur = self_next;
+    }
+}
+
 template <int P, bool kKahan>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *items, const int *off, const int4 *rng,
-                                                     const float4 *pos, const float4 *geom, const int *level,
-                                                     const float *L, const int *perm, float phi_scale,
-                                                     float grad_scale, float *phi, float *grad, float *phi_sorted)
+__global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nitems, const int4 *items, const unsigned *roff,
+                                                     const float4 *run, const int *run_end, const float4 *pos,
+                                                     const int *pbeg, const int *pcnt, const int *level,
+                                                     const int *parent, const float4 *geom, const float *L,
+                                                     const int *perm, float phi_scale, float grad_scale, float *phi,
+                                                     float *grad, float *phi_sorted)
 {
     constexpr int G = kP2PG;
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
+    extern __shared__ float4 p2p_smem[];
     const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= nitems) return;
     const unsigned lane = lane_id();
+    float4 *buf = p2p_smem + (threadIdx.x >> 5) * (4 * kSlots);   // [2][particles, shifts][kSlots]
     const int4 it = items[item];
     const int leaf = it.x, tb = it.y, tc = it.z;
+    const int lb0 = pbeg[leaf], lb1 = lb0 + pcnt[leaf];   // the target leaf's own particles
 
-    // targets and sources are offsets from their leaf centres; a source of leaf S
-    // is moved into the target leaf's frame by the exact shift X_S - X_T
-    const float4 Xt = geom[leaf];
-    float tx[G], ty[G], tz[G];
+    // targets (offsets from the target frame centre, warp-uniform), negated, in
+    // float2 pairs; extra slots repeat the last target
+    float2 ntx[G / 2], nty[G / 2], ntz[G / 2];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const float4 p = pos[tb + min(g, tc - 1)];
-        tx[g] = p.x;
-        ty[g] = p.y;
-        tz[g] = p.z;
+    for (int h = 0; h < G / 2; ++h) {
+        const float4 p0 = pos[tb + min(2 * h, tc - 1)];
+        const float4 p1 = pos[tb + min(2 * h + 1, tc - 1)];
+        ntx[h] = make_float2(-p0.x, -p1.x);
+        nty[h] = make_float2(-p0.y, -p1.y);
+        ntz[h] = make_float2(-p0.z, -p1.z);
     }
-    // acc layout: v[4 g + 0] potential, v[4 g + 1..3] gradient
+    // a[4 h + k]: component k (potential, gradient x, y, z) of targets 2h, 2h+1
+    float2 a[2 * G];
+#pragma unroll
+    for (int i = 0; i < 2 * G; ++i) a[i] = make_float2(0.0f, 0.0f);
+    float2 comp[kKahan ? 2 * G : 1];
+    float2 blk[kKahan ? 2 * G : 1];
+    if (kKahan) {
+#pragma unroll
+        for (int i = 0; i < 2 * G; ++i) comp[i] = blk[i] = make_float2(0.0f, 0.0f);
+    }
+
+    RunCursor cur;
+    cur.e = (int)roff[it.w];
+    cur.e1 = (int)roff[it.w + 1];
+    cur.o = 0;
+    cur.pb = 0;
+    cur.cnt = 0;
+    cur.shx = cur.shy = cur.shz = 0.f;
+    cur.load(run, run_end);
+    // the item computes ceil(tc / 4) * 4 targets (extra ones repeat the last target)
+    switch ((tc + 3) >> 2) {
+    case 1: p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    case 2: p2p_stream<8, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    case 3: p2p_stream<12, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    default: p2p_stream<16, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    }
+    // v[4 g + k]: component k of target g
     float v[4 * G];
 #pragma unroll
-    for (int i = 0; i < 4 * G; ++i) v[i] = 0.0f;
-    float comp[kKahan ? 4 * G : 1];
-    float blk[kKahan ? 4 * G : 1];
-    if (kKahan) {
+    for (int h = 0; h < G / 2; ++h)
 #pragma unroll
-        for (int i = 0; i < 4 * G; ++i) comp[i] = blk[i] = 0.0f;
-    }
-
-    // per-lane cursor over the concatenated source particles of the item's list:
-    // entry e, offset o inside it, its range r and its frame shift
-    const int e1 = off[leaf + 1];
-    int e = off[leaf];
-    int o = (int)lane;
-    int4 r = make_int4(0, 0, 0, 0);
-    float shx = 0.f, shy = 0.f, shz = 0.f;
-    bool fresh = true;
-    for (;;) {
-        if (fresh) r = e < e1 ? rng[e] : make_int4(0, 0, 0, 0);
-        if (e < e1 && o >= r.y) {
-            o -= r.y;
-            ++e;
-            fresh = true;
-            continue;
+        for (int k = 0; k < 4; ++k) {
+            v[4 * (2 * h) + k] = a[4 * h + k].x;
+            v[4 * (2 * h + 1) + k] = a[4 * h + k].y;
         }
-        break;
-    }
-    if (e < e1) {
-        const float4 Xs = geom[r.z];
-        shx = Xs.x - Xt.x;
-        shy = Xs.y - Xt.y;
-        shz = Xs.z - Xt.z;
-    }
-    int nsub = 0;
-    while (__any_sync(kFull, e < e1)) {
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (e < e1) {
-            s = pos[r.x + o];
-            s.x += shx;
-            s.y += shy;
-            s.z += shz;
-        }
-#pragma unroll
-        for (int sb = 0; sb < G / 4; ++sb) {
-            if (4 * sb < tc) {
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) {
-                    const int g = 4 * sb + gg;
-                    const float dx = s.x - tx[g], dy = s.y - ty[g], dz = s.z - tz[g];
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    float rinv = rsqrtf(r2);
-                    rinv = r2 > 0.0f ? rinv : 0.0f;
-                    const float qr = s.w * rinv;
-                    const float qr3 = qr * rinv * rinv;
-                    float *acc = kKahan ? blk : v;
-                    acc[4 * g + 0] += qr;
-                    acc[4 * g + 1] = fmaf(qr3, dx, acc[4 * g + 1]);
-                    acc[4 * g + 2] = fmaf(qr3, dy, acc[4 * g + 2]);
-                    acc[4 * g + 3] = fmaf(qr3, dz, acc[4 * g + 3]);
-                }
-            }
-        }
-        if (kKahan && ++nsub == 8) {
-            nsub = 0;
-#pragma unroll
-            for (int i = 0; i < 4 * G; ++i) {
-                const float y = blk[i] - comp[i];
-                const float t = v[i] + y;
-                comp[i] = (t - v[i]) - y;
-                v[i] = t;
-                blk[i] = 0.0f;
-            }
-        }
-        o += 32;
-        if (e < e1 && o >= r.y) {
-            do {
-                o -= r.y;
-                ++e;
-                r = e < e1 ? rng[e] : make_int4(0, 0, 0, 0);
-            } while (e < e1 && o >= r.y);
-            if (e < e1) {
-                const float4 Xs = geom[r.z];
-                shx = Xs.x - Xt.x;
-                shy = Xs.y - Xt.y;
-                shz = Xs.z - Xt.z;
-            }
-        }
-    }
-    if (kKahan) {
-#pragma unroll
-        for (int i = 0; i < 4 * G; ++i) {
-            const float y = blk[i] - comp[i];
-            v[i] = v[i] + y;
-        }
-    }
 
     warp_reduce_scatter64(v);
     // lane 2g holds (phi, gx) of target g, lane 2g+1 holds (gy, gz)
@@ -216,11 +363,14 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
     const float4 p = pos[sidx];
     float pot = v[0], gx = v[1], gy = o0, gz = o1;
 
-    // L2P: phi += sum_n Lb_n w_n(r / s), grad += (1/s) sum_m Lb_{m + e_d} w_m(r / s), r = p (leaf offset)
+    // L2P: phi += sum_n Lb_n w_n(r / s), grad += (1/s) sum_m Lb_{m + e_d} w_m(r / s),
+    // r = u - X_leaf = d - (X_leaf - X_frame)
     {
         const float inv_s = ldexpf(1.0f, level[leaf]);
+        const float4 Xc = geom[leaf], Xf = geom[frame_of(parent, leaf)];
         float w[T];
-        taylor_monomials<P>(p.x * inv_s, p.y * inv_s, p.z * inv_s, w);
+        taylor_monomials<P>(fmaf(p.x, inv_s, -(Xc.x - Xf.x) * inv_s), fmaf(p.y, inv_s, -(Xc.y - Xf.y) * inv_s),
+                            fmaf(p.z, inv_s, -(Xc.z - Xf.z) * inv_s), w);
         const float *Lc = L + (size_t)leaf * TP;
         float lp = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
 #pragma unroll
@@ -257,8 +407,26 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(int nitems, const int4 *ite
 int build_p2p_items(Handle &h)
 {
     const int nl = (int)h.nleaves;
-    FMM_TRY(h.c_tmp.reserve((size_t)(2 * nl + 1) * sizeof(unsigned)));
-    unsigned *cnt = h.c_tmp.as<unsigned>(), *off = cnt + nl, *tot = off + nl;
+    FMM_TRY(h.c_tmp.reserve((size_t)(4 * nl + 2) * sizeof(unsigned)));
+    unsigned *cnt = h.c_tmp.as<unsigned>(), *off = cnt + nl, *tot = off + nl, *nrun = tot + 1;
+    FMM_TRY(h.p2p_poff.reserve((size_t)(nl + 1) * sizeof(unsigned)));
+    unsigned *roff = h.p2p_poff.as<unsigned>();
+    // source runs of every target leaf's list
+    ++h.launches;
+    k_p2p_run_count<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
+        nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.c_parent.as<int>(), h.c_pbeg.as<int>(),
+        h.c_pcnt.as<int>(), nrun);
+    FMM_TRY(scan_exclusive_u32(h, nrun, roff, nl, roff + nl));
+    FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, roff + nl, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    h.n_pieces = h.pinned->level_total;
+    FMM_TRY(h.p2p_ent.reserve(std::max<int64_t>(h.n_pieces, 1) * sizeof(float4)));
+    FMM_TRY(h.p2p_cnt.reserve(std::max<int64_t>(h.n_pieces, 1) * sizeof(int)));
+    ++h.launches;
+    k_p2p_runs<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
+        nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.c_parent.as<int>(), h.c_pbeg.as<int>(),
+        h.c_pcnt.as<int>(), h.c_geom.as<float4>(), roff, h.p2p_ent.as<float4>(), h.p2p_cnt.as<int>());
+    // work items
     ++h.launches;
     k_p2p_item_count<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pcnt.as<int>(), cnt);
     FMM_TRY(scan_exclusive_u32(h, cnt, off, nl, tot));
@@ -269,36 +437,34 @@ int build_p2p_items(Handle &h)
     ++h.launches;
     k_p2p_item_write<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
                                                               h.c_pcnt.as<int>(), off, h.p2p_items.as<int4>());
-    FMM_TRY(h.p2p_rng.reserve(std::max<int64_t>(h.n_p2p, 1) * sizeof(int4)));
-    if (h.n_p2p > 0) {
-        ++h.launches;
-        k_p2p_ranges<<<ceil_div(h.n_p2p, 256), 256, 0, h.stream>>>(h.n_p2p, h.p2p_src.as<int>(), h.c_pbeg.as<int>(),
-                                                                 h.c_pcnt.as<int>(), h.p2p_rng.as<int4>());
-    }
     FMM_CHECK_LAUNCH("p2p items");
+    return FMM_OK;
+}
+
+template <int P, bool kKahan> static int p2p_launch(Handle &h, float *phi, float *grad)
+{
+    static bool configured[64] = {};
+    if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
+        FMM_CUDA(cudaFuncSetAttribute(k_p2p<P, kKahan>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2PSmem));
+        configured[h.device] = true;
+    }
+    const float phi_scale = (float)(1.0 / h.norm_host[3]);
+    const float grad_scale = (float)(1.0 / (h.norm_host[3] * h.norm_host[3]));
+    const int blocks = ceil_div((int64_t)h.n_items * 32, kP2PThreads);
+    ++h.launches;
+    k_p2p<P, kKahan><<<blocks, kP2PThreads, kP2PSmem, h.stream>>>(
+        (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
+        h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
+        h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
+        grad, h.phi_sorted.as<float>());
+    FMM_CHECK_LAUNCH("p2p");
     return FMM_OK;
 }
 
 template <int P> static int p2p_impl(Handle &h, float *phi, float *grad)
 {
-    const float phi_scale = (float)(1.0 / h.norm_host[3]);
-    const float grad_scale = (float)(1.0 / (h.norm_host[3] * h.norm_host[3]));
-    const int blocks = ceil_div((int64_t)h.n_items * 32, kP2PThreads);
-    if (h.flags & FMM_FLAG_KAHAN) {
-        ++h.launches;
-        k_p2p<P, true><<<blocks, kP2PThreads, 0, h.stream>>>(
-            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int4>(), h.pos.as<float4>(),
-            h.c_geom.as<float4>(), h.c_level.as<int>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
-            grad, h.phi_sorted.as<float>());
-    } else {
-        ++h.launches;
-        k_p2p<P, false><<<blocks, kP2PThreads, 0, h.stream>>>(
-            (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_off.as<int>(), h.p2p_rng.as<int4>(), h.pos.as<float4>(),
-            h.c_geom.as<float4>(), h.c_level.as<int>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
-            grad, h.phi_sorted.as<float>());
-    }
-    FMM_CHECK_LAUNCH("p2p");
-    return FMM_OK;
+    if (h.flags & FMM_FLAG_KAHAN) return p2p_launch<P, true>(h, phi, grad);
+    return p2p_launch<P, false>(h, phi, grad);
 }
 
 int evaluate_p2p(Handle &h, float *phi, float *grad)

@@ -372,18 +372,23 @@ __global__ void k_radius_final(int nc, const unsigned *r2bits, float4 *geom)
     geom[c].w = __fsqrt_rn(__uint_as_float(r2bits[c]));
 }
 
-// Particle positions stored as FP32 offsets from the centre of their leaf,
-// d = u - X_leaf, rounded once from FP64 (u recomputed exactly as for the keys).
-// Leaf centres are exact in FP32, so the kernels recover differences of nearby
-// particles to ~2^-24 of the leaf size instead of 2^-24 of the domain size.
+// Particle positions are stored as FP32 offsets from the centre of their
+// leaf's parent (the "frame" cell; the root frames itself), d = u - X_frame,
+// rounded once from FP64 (u recomputed exactly as for the keys).  Cell centres
+// are exact in FP32, so kernels recover differences of nearby particles to
+// ~2^-24 of the frame size instead of 2^-24 of the domain size; sibling leaves
+// share a frame, so a run of consecutive siblings is one contiguous block of
+// particles in one frame.
 __global__ void k_local_positions(const double *x, int64_t n, const int *perm, const double *norm, const int *leaf_of,
-                                  const float4 *geom, float4 *pos)
+                                  const int *parent, const float4 *geom, float4 *pos)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
     const double h = norm[3];
-    const float4 X = geom[leaf_of[s]];
+    const int lf = leaf_of[s];
+    const int fr = parent[lf] >= 0 ? parent[lf] : lf;
+    const float4 X = geom[fr];
     const double cx = X.x, cy = X.y, cz = X.z;
     const double ux = __ddiv_rn(__dsub_rn(x[3 * i + 0], norm[0]), h);
     const double uy = __ddiv_rn(__dsub_rn(x[3 * i + 1], norm[1]), h);
@@ -471,11 +476,11 @@ int build_tree(Handle &h, const double *x)
         h.c_r2bits.as<unsigned>());
     ++h.launches;
     k_radius_final<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_r2bits.as<unsigned>(), h.c_geom.as<float4>());
-    // from here on particles are stored relative to their leaf centre
+    // from here on particles are stored relative to the centre of their leaf's parent
     ++h.launches;
     k_local_positions<<<ceil_div(N, 256), 256, 0, h.stream>>>(x, N, h.perm.as<int>(), h.norm.as<double>(),
-                                                              h.leaf_of.as<int>(), h.c_geom.as<float4>(),
-                                                              h.pos.as<float4>());
+                                                              h.leaf_of.as<int>(), h.c_parent.as<int>(),
+                                                              h.c_geom.as<float4>(), h.pos.as<float4>());
     FMM_CHECK_LAUNCH("geometry");
     phase_end(h, FMM_PHASE_TREE);
     return FMM_OK;
