@@ -9,12 +9,16 @@
 //
 // Kernel layout:
 //   P2M  one warp per leaf, lanes over its particles, warp reduction;
-//   M2M  one thread per cell of a level, sum over its children (bottom-up);
+//   M2M  one thread per cell of a level (P <= 6) or one warp per cell over a
+//        term table (P = 8), summing its children (bottom-up);
 //   M2L  one warp per target cell, lanes over its M2L sources, each lane
 //        computing the kernel derivatives D_m(R) of its pair and contracting,
 //        then a warp reduction of the T local coefficients;
 //   L2L  one thread per cell of a level, from its parent (top-down).
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "device_util.cuh"
 #include "fmm_internal.cuh"
@@ -76,6 +80,7 @@ __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const 
 // M2M: Mb_k(P) = sum_{m <= k} Mb_m(C) 2^-|m| w_{k-m}((X_P - X_C) / s_P)
 // (child half-width s_C = s_P / 2, (X_P - X_C) / s_P = -(+-1/2) per axis)
 // ---------------------------------------------------------------------------
+// P <= 6: one thread per cell of a level, fully unrolled.
 template <int P>
 __global__ void k_m2m(int lo, int n, const int *cbeg, const int *ccnt, const float4 *geom, float *M)
 {
@@ -98,7 +103,6 @@ __global__ void k_m2m(int lo, int n, const int *cbeg, const int *ccnt, const flo
         const float *src = M + (size_t)ch * TP;
 #pragma unroll
         for (int t = 0; t < T; ++t) mc[t] = src[t];
-        // acc_k += sum_{m <= k} mc_m 2^-|m| w_{k-m}
 #pragma unroll
         for (int nk = 0; nk < P; ++nk)
 #pragma unroll
@@ -124,55 +128,149 @@ __global__ void k_m2m(int lo, int n, const int *cbeg, const int *ccnt, const flo
     for (int t = 0; t < TP; ++t) dst[t] = t < T ? acc[t] : 0.0f;
 }
 
-// ---------------------------------------------------------------------------
-// M2L: Lb_n(T) = (1/s_T) sum_S sum_k (s_S/s_T)^|k| Mb_k(S) D_{n+k}((X_T - X_S)/s_T)
-// ---------------------------------------------------------------------------
+// Higher orders: one warp per cell, lanes over the terms (k, m) of the shift
+// from a term table.  With s the child's octant signs, the factor of a term is
+// 2^-|k| prod_i (-s_i)^(j_i) / j_i!, j = k - m: the table holds k, m, the parity
+// of j per axis and 1/j!; the sign and 2^-|k| are applied here.  The table is
+// ordered m-major, so the 32 lanes of a step add into distinct outputs k of a
+// shared-memory accumulator.
+struct M2MTerm {
+    unsigned kmp;   // k | m << 8 | (j_x odd, j_y odd, j_z odd) << 16
+    float coef;     // 1 / (j_x! j_y! j_z!)
+};
+
 template <int P>
-__global__ void __launch_bounds__(128) k_m2l(int ncells, const int *off, const int *src, const int *level,
-                                             const float4 *geom, const float *M, float *L)
+__global__ void __launch_bounds__(128) k_m2m_table(int lo, int n, const int *cbeg, const int *ccnt,
+                                                   const float4 *geom, const M2MTerm *terms, int nterms, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= ncells) return;
+    __shared__ float acc_s[4][TP];
+    const int w = threadIdx.x >> 5;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = (int)lane_id();
+    if (i >= n) return;
+    const int c = lo + i;
+    const int nch = ccnt[c];
+    if (nch == 0) return;
+    float *acc = acc_s[w];
+    for (int k = lane; k < TP; k += 32) acc[k] = 0.0f;
+    __syncwarp();
+    const float4 Xp = geom[c];
+    for (int q = 0; q < nch; ++q) {
+        const int ch = cbeg[c] + q;
+        const float4 Xc = geom[ch];
+        const unsigned flip = (Xc.x > Xp.x ? 1u : 0u) | (Xc.y > Xp.y ? 2u : 0u) | (Xc.z > Xp.z ? 4u : 0u);
+        const float *mc = M + (size_t)ch * TP;
+        for (int t = lane; t < nterms; t += 32) {
+            const M2MTerm e = terms[t];
+            const unsigned k = e.kmp & 0xffu, m = (e.kmp >> 8) & 0xffu, par = e.kmp >> 16;
+            const float v = __ldg(mc + m) * ((__popc(par & flip) & 1) ? -e.coef : e.coef);
+            atomicAdd(acc + k, v);
+        }
+    }
+    __syncwarp();
+    float *dst = M + (size_t)c * TP;
+    for (int k = lane; k < TP; k += 32) {
+        if (k < T) {
+            int n_deg = 0;
+            while ((n_deg + 1) * (n_deg + 2) * (n_deg + 3) / 6 <= k) ++n_deg;
+            dst[k] = ldexpf(acc[k], -n_deg);
+        } else {
+            dst[k] = 0.0f;
+        }
+    }
+}
+
+// Host: the term table of order P, m-major.
+static std::vector<M2MTerm> m2m_term_table(int P)
+{
+    auto idx = [](int a, int b, int c) {
+        const int n = a + b + c, bc = b + c;
+        return n * (n + 1) * (n + 2) / 6 + bc * (bc + 1) / 2 + c;
+    };
+    double fact[16];
+    fact[0] = 1.0;
+    for (int i = 1; i < 16; ++i) fact[i] = fact[i - 1] * i;
+    std::vector<M2MTerm> out;
+    for (int mn = 0; mn < P; ++mn)
+        for (int ma = mn; ma >= 0; --ma)
+            for (int mb = mn - ma; mb >= 0; --mb) {
+                const int mc = mn - ma - mb;
+                for (int kn = mn; kn < P; ++kn)
+                    for (int ka = kn; ka >= 0; --ka)
+                        for (int kb = kn - ka; kb >= 0; --kb) {
+                            const int kc = kn - ka - kb;
+                            if (ka < ma || kb < mb || kc < mc) continue;
+                            const int ja = ka - ma, jb = kb - mb, jc = kc - mc;
+                            M2MTerm e;
+                            e.kmp = (unsigned)idx(ka, kb, kc) | ((unsigned)idx(ma, mb, mc) << 8) |
+                                    ((unsigned)((ja & 1) | ((jb & 1) << 1) | ((jc & 1) << 2)) << 16);
+                            e.coef = (float)(1.0 / (fact[ja] * fact[jb] * fact[jc]));
+                            out.push_back(e);
+                        }
+            }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// M2L: Lb_n(T) = (1/s_T) sum_S sum_k (s_S/s_T)^|k| Mb_k(S) D_{n+k}((X_T - X_S)/s_T)
+// One warp per target cell, lanes over its M2L sources; each lane computes the
+// kernel derivatives of its pair and contracts them with the source multipole
+// into the output coefficients N0 <= idx(n) < N1 (all of them for P <= 6; for
+// P = 8 two passes over the sources, each recomputing D, keep everything in
+// registers), then the warp sums its lanes.
+// ---------------------------------------------------------------------------
+template <int P, int N0, int N1>
+__device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, const int *level, const float4 *geom,
+                                         const float *M, float *L)
+{
+    constexpr int T = MI<P>::T, TP = MI<P>::TP, NO = N1 - N0;
     const float4 Xt = geom[t];
     const int lt = level[t];
     const float inv_st = ldexpf(1.0f, lt);
-    float acc[T];
+    float acc[NO];
 #pragma unroll
-    for (int i = 0; i < T; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < NO; ++i) acc[i] = 0.0f;
     const int b = off[t], e = off[t + 1];
     for (int k = b + (int)lane_id(); k < e; k += 32) {
         const int s = src[k];
         const float4 Xs = geom[s];
-        const float rho = ldexpf(1.0f, lt - level[s]);   // s_S / s_T
         float D[T];
         laplace_derivatives<P>((Xt.x - Xs.x) * inv_st, (Xt.y - Xs.y) * inv_st, (Xt.z - Xs.z) * inv_st, D);
-        float Mk[T];
-        const float4 *m4 = reinterpret_cast<const float4 *>(M + (size_t)s * TP);
+        const float rho = ldexpf(1.0f, lt - level[s]);   // s_S / s_T
+        float rho_pow[P];
+        rho_pow[0] = 1.0f;
 #pragma unroll
-        for (int i = 0; i < TP / 4; ++i) {
-            const float4 v = __ldg(m4 + i);
-            if (4 * i + 0 < T) Mk[4 * i + 0] = v.x;
-            if (4 * i + 1 < T) Mk[4 * i + 1] = v.y;
-            if (4 * i + 2 < T) Mk[4 * i + 2] = v.z;
-            if (4 * i + 3 < T) Mk[4 * i + 3] = v.w;
-        }
-        if (rho != 1.0f) {
-            float r = rho;
-#pragma unroll
-            for (int nk = 1; nk < P; ++nk) {
-#pragma unroll
-                for (int i = MI<P>::idx(nk, 0, 0); i < MI<P>::idx(nk, 0, 0) + (nk + 1) * (nk + 2) / 2; ++i)
-                    Mk[i] *= r;
-                r *= rho;
-            }
-        }
-        m2l_contract<P>(Mk, D, acc);
+        for (int d = 1; d < P; ++d) rho_pow[d] = rho_pow[d - 1] * rho;
+        m2l_contract_range<P, N0, N1>(reinterpret_cast<const float4 *>(M + (size_t)s * TP), rho_pow, D, acc);
     }
-    warp_reduce_vec<T>(acc);
 #pragma unroll
-    for (int i = 0; i < T; ++i) acc[i] *= inv_st;
-    warp_store_vec<T, TP>(acc, L + (size_t)t * TP);
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < NO; ++i) acc[i] += __shfl_xor_sync(kFull, acc[i], o);
+    float *dst = L + (size_t)t * TP;
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int i = 0; i < NO; ++i)
+        if ((i & 31) == lane) dst[N0 + i] = acc[i] * inv_st;
+    if (N1 == T)
+        for (int i = T + lane; i < TP; i += 32) dst[i] = 0.0f;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2l(int ncells, const int *off, const int *src, const int *level,
+                                             const float4 *geom, const float *M, float *L)
+{
+    constexpr int T = MI<P>::T;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= ncells) return;
+    if constexpr (P >= 8) {
+        constexpr int split = MI<P>::idx(5, 0, 0);   // outputs of degree <= 4 | degree >= 5
+        m2l_pass<P, 0, split>(t, off, src, level, geom, M, L);
+        m2l_pass<P, split, T>(t, off, src, level, geom, M, L);
+    } else {
+        m2l_pass<P, 0, T>(t, off, src, level, geom, M, L);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -235,11 +333,23 @@ template <int P> static int upward_impl(Handle &h, const float *q)
                                                                     h.c_pcnt.as<int>(), h.c_level.as<int>(),
                                                                     h.c_parent.as<int>(), h.c_geom.as<float4>(),
                                                                     h.pos.as<float4>(), h.M.as<float>());
+    if (P >= 8 && h.m2m_nterms == 0) {
+        const std::vector<M2MTerm> tab = m2m_term_table(P);
+        FMM_TRY(h.m2m_terms.reserve(tab.size() * sizeof(M2MTerm)));
+        FMM_CUDA(cudaMemcpy(h.m2m_terms.p, tab.data(), tab.size() * sizeof(M2MTerm), cudaMemcpyHostToDevice));
+        h.m2m_nterms = (int)tab.size();
+    }
+    const int nterms = h.m2m_nterms;
     for (int l = h.nlevels - 2; l >= 0; --l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
         ++h.launches;
-        k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
-                                                       h.c_geom.as<float4>(), h.M.as<float>());
+        if (P >= 8)
+            k_m2m_table<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
+                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), h.m2m_terms.as<M2MTerm>(),
+                nterms, h.M.as<float>());
+        else
+            k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
+                                                           h.c_geom.as<float4>(), h.M.as<float>());
     }
     FMM_CHECK_LAUNCH("upward pass");
     return FMM_OK;

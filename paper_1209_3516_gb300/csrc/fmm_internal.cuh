@@ -144,6 +144,8 @@ struct Handle {
 
     // expansions and outputs
     DevBuf M, L;          // float[ncells * TP]
+    DevBuf m2m_terms;     // term table of the high-order M2M kernel
+    int m2m_nterms = 0;
     DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
     DevBuf energy_part;   // double partials
 
@@ -168,6 +170,7 @@ int radix_sort_pairs(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *
                      unsigned *&vals_alt, int64_t n, int begin_bit, int end_bit);
 int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, int begin_bit,
                     int end_bit);
+int radix_sort_keys32(Handle &h, uint32_t *&keys, uint32_t *&keys_alt, int64_t n, int begin_bit, int end_bit);
 
 int build_keys(Handle &h, const double *x);       // bbox, normalise, Morton, sort, gather
 int build_tree(Handle &h, const double *x);       // cells, geometry, leaf-local positions

@@ -113,4 +113,37 @@ __device__ __forceinline__ void m2l_contract(const float *Mk, const float *D, fl
             }
 }
 
+// acc[idx(n) - N0] += sum_{|k| <= P-1-|n|} rho^|k| M[idx(k)] D[idx(n+k)] for the
+// outputs with N0 <= idx(n) < N1; M is read from global memory (float4-aligned,
+// TP floats) while the contraction runs, so only D and the accumulators of
+// this output range stay in registers.
+template <int P, int N0, int N1>
+__device__ __forceinline__ void m2l_contract_range(const float4 *M4, const float *rho_pow, const float *D, float *acc)
+{
+    float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int nk = 0; nk < P; ++nk)
+#pragma unroll
+        for (int ka = nk; ka >= 0; --ka)
+#pragma unroll
+            for (int kb = nk - ka; kb >= 0; --kb) {
+                const int kc = nk - ka - kb;
+                const int ik = MI<P>::idx(ka, kb, kc);
+                if ((ik & 3) == 0) m4 = __ldg(M4 + (ik >> 2));
+                const float mraw = (ik & 3) == 0 ? m4.x : (ik & 3) == 1 ? m4.y : (ik & 3) == 2 ? m4.z : m4.w;
+                const float m = mraw * rho_pow[nk];
+#pragma unroll
+                for (int nn = 0; nn + nk < P; ++nn)
+#pragma unroll
+                    for (int na = nn; na >= 0; --na)
+#pragma unroll
+                        for (int nb = nn - na; nb >= 0; --nb) {
+                            const int nc = nn - na - nb;
+                            const int in = MI<P>::idx(na, nb, nc);
+                            if (in >= N0 && in < N1)
+                                acc[in - N0] = fmaf(m, D[MI<P>::idx(na + ka, nb + kb, nc + kc)], acc[in - N0]);
+                        }
+            }
+}
+
 }  // namespace fmm

@@ -12,7 +12,8 @@
 //     with cp.async so the next chunk streams in while the current one is
 //     used; each lane takes one staged source per step and computes its 16
 //     pair interactions, two targets per packed FP32 instruction (FFMA2,
-//     FADD2, FMUL2) and one SFU rsqrt per pair;
+//     FADD2, FMUL2) and one SFU rsqrt per pair (13 FP32 operations, 6.5 issue
+//     slots, 1 SFU operation per pair);
 //   - positions are FP32 offsets from the centre of the leaf's parent (the
 //     frame); a source is moved into the target's frame by the exact (dyadic)
 //     shift X_frame(S) - X_frame(T), so close pairs keep ~2^-24 of the frame
@@ -33,7 +34,10 @@
 
 namespace fmm {
 
-constexpr int kP2PG = 16;          // targets per work item
+#ifndef FMM_P2P_G
+#define FMM_P2P_G 16
+#endif
+constexpr int kP2PG = FMM_P2P_G;   // targets per work item (multiple of 4, at most 16)
 constexpr int kP2PThreads = 128;
 
 #ifndef FMM_P2P_SLOTS
@@ -42,7 +46,11 @@ constexpr int kP2PThreads = 128;
 #ifndef FMM_P2P_MIN_BLOCKS
 #define FMM_P2P_MIN_BLOCKS 3
 #endif
+#ifndef FMM_P2P_UNROLL
+#define FMM_P2P_UNROLL 1
+#endif
 constexpr int kSlots = FMM_P2P_SLOTS;   // staged source particles per buffer
+constexpr int kP2PUnroll = FMM_P2P_UNROLL;   // staged sources per lane per loop iteration
 constexpr int kP2PSmem = (kP2PThreads / 32) * 4 * kSlots * (int)sizeof(float4);   // 2 buffers x (particles + shifts)
 
 __device__ __forceinline__ int frame_of(const int *parent, int c) { return parent[c] >= 0 ? parent[c] : c; }
@@ -151,28 +159,30 @@ __device__ __forceinline__ void warp_reduce_scatter64(float *v)
 // NT targets, two targets per packed FP32 instruction (FFMA2 / FADD2 / FMUL2):
 // targets are held negated as float2 pairs (ntx[h] = -(t_2h, t_2h+1)), and
 // acc[4h + k] is component k (potential, gradient x, y, z) of that pair.
-// kExact: pairs at distance 0 contribute exactly nothing (needed where a
-// particle meets itself, in chunks holding the target leaf's own particles);
-// otherwise r^2 is clamped to FLT_MIN, which only matters for two distinct
-// particles that round to the same FP32 point and costs one instruction
-// instead of two.
+// r^2 is accumulated on top of eps = FLT_MIN, which keeps rsqrt finite and
+// leaves every squared distance representable in FP32 unchanged (only pairs
+// that round to the same FP32 point see it).  kExact (chunks holding the target
+// leaf's own particles): a pair at distance 0 (a particle meeting itself, or a
+// coincident one) has r^2 = eps and contributes exactly nothing.
 template <int NT, bool kExact>
 __device__ __forceinline__ void p2p_tile(const float4 &s, const float2 *ntx, const float2 *nty, const float2 *ntz,
                                          float2 *acc)
 {
+    constexpr float kEps = 1.17549435e-38f;
     const float2 sx = make_float2(s.x, s.x), sy = make_float2(s.y, s.y), sz = make_float2(s.z, s.z);
     const float2 sq = make_float2(s.w, s.w);
+    const float2 eps = make_float2(kEps, kEps);
 #pragma unroll
     for (int h = 0; h < NT / 2; ++h) {
         const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps)));
         float2 rinv;
         if (kExact) {
-            rinv.x = r2.x > 0.0f ? rsqrt_approx(r2.x) : 0.0f;
-            rinv.y = r2.y > 0.0f ? rsqrt_approx(r2.y) : 0.0f;
+            rinv.x = r2.x > kEps ? rsqrt_approx(r2.x) : 0.0f;
+            rinv.y = r2.y > kEps ? rsqrt_approx(r2.y) : 0.0f;
         } else {
-            rinv.x = rsqrt_approx(fmaxf(r2.x, 1.17549435e-38f));
-            rinv.y = rsqrt_approx(fmaxf(r2.y, 1.17549435e-38f));
+            rinv.x = rsqrt_approx(r2.x);
+            rinv.y = rsqrt_approx(r2.y);
         }
         const float2 qr = __fmul2_rn(sq, rinv);
         const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(rinv, rinv));
@@ -258,6 +268,7 @@ __device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, co
         cp_async_wait_1();
         __syncwarp();
         float2 *acc = kKahan ? blk : v;
+#pragma unroll kP2PUnroll
         for (int t0 = 0; t0 < n_cur; t0 += 32) {
             const int j = t0 + lane;
             float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -340,11 +351,13 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     switch ((tc + 3) >> 2) {
     case 1: p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
     case 2: p2p_stream<8, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
-    case 3: p2p_stream<12, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
-    default: p2p_stream<16, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    case 3: p2p_stream<(G >= 12 ? 12 : 8), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    default: p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
     }
-    // v[4 g + k]: component k of target g
-    float v[4 * G];
+    // v[4 g + k]: component k of target g (zero-padded to 16 targets)
+    float v[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.0f;
 #pragma unroll
     for (int h = 0; h < G / 2; ++h)
 #pragma unroll

@@ -143,7 +143,8 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per tile
 
-__global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const uint64_t *keys, int64_t n, int shift, int ntiles,
+template <class K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *keys, int64_t n, int shift, int ntiles,
                                                            unsigned *hist)
 {
     __shared__ unsigned cnt[256];
@@ -159,10 +160,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const uint64_t *keys,
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-template <bool kVals>
-__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *keys, const unsigned *vals, int64_t n,
+template <class K, bool kVals>
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *keys, const unsigned *vals, int64_t n,
                                                            int shift, int ntiles, const unsigned *offsets,
-                                                           uint64_t *keys_out, unsigned *vals_out)
+                                                           K *keys_out, unsigned *vals_out)
 {
     __shared__ unsigned s_base[256];
     __shared__ unsigned s_cnt[kRsWarps][256];
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *keys,
     for (int r = 0; r < kRsRounds; ++r) {
         const int64_t i = base + r * kRsThreads + t;
         const bool valid = i < n;
-        uint64_t key = valid ? keys[i] : 0ull;
+        K key = valid ? keys[i] : (K)0;
         unsigned val = 0;
         if (kVals && valid) val = vals[i];
         const unsigned d = valid ? ((unsigned)(key >> shift) & 0xffu) : 256u;
@@ -204,8 +205,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t *keys,
     }
 }
 
-static int radix_sort_impl(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals,
-                           unsigned *&vals_alt, bool with_vals, int64_t n, int begin_bit, int end_bit)
+template <class K>
+static int radix_sort_impl(Handle &h, K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_alt, bool with_vals,
+                           int64_t n, int begin_bit, int end_bit)
 {
     if (n <= 1 || end_bit <= begin_bit) return FMM_OK;
     if (n > 0xffffffffll) {
@@ -219,20 +221,20 @@ static int radix_sort_impl(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsi
     unsigned *offs = hist + nh;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         ++h.launches;
-        k_rs_upsweep<<<ntiles, kRsThreads, 0, h.stream>>>(keys, n, shift, ntiles, hist);
+        k_rs_upsweep<K><<<ntiles, kRsThreads, 0, h.stream>>>(keys, n, shift, ntiles, hist);
         FMM_CHECK_LAUNCH("radix upsweep");
         FMM_TRY(scan_exclusive_u32(h, hist, offs, nh, nullptr));
         if (with_vals) {
             ++h.launches;
-            k_rs_scatter<true><<<ntiles, kRsThreads, 0, h.stream>>>(keys, vals, n, shift, ntiles, offs, keys_alt,
-                                                                  vals_alt);
+            k_rs_scatter<K, true><<<ntiles, kRsThreads, 0, h.stream>>>(keys, vals, n, shift, ntiles, offs, keys_alt,
+                                                                     vals_alt);
         } else {
             ++h.launches;
-            k_rs_scatter<false><<<ntiles, kRsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ntiles, offs,
-                                                                   keys_alt, nullptr);
+            k_rs_scatter<K, false><<<ntiles, kRsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ntiles, offs,
+                                                                      keys_alt, nullptr);
         }
         FMM_CHECK_LAUNCH("radix scatter");
-        uint64_t *tk = keys;
+        K *tk = keys;
         keys = keys_alt;
         keys_alt = tk;
         if (with_vals) {
@@ -247,13 +249,19 @@ static int radix_sort_impl(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsi
 int radix_sort_pairs(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals, unsigned *&vals_alt,
                      int64_t n, int begin_bit, int end_bit)
 {
-    return radix_sort_impl(h, keys, keys_alt, vals, vals_alt, true, n, begin_bit, end_bit);
+    return radix_sort_impl<uint64_t>(h, keys, keys_alt, vals, vals_alt, true, n, begin_bit, end_bit);
 }
 
 int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, int begin_bit, int end_bit)
 {
     unsigned *a = nullptr, *b = nullptr;
-    return radix_sort_impl(h, keys, keys_alt, a, b, false, n, begin_bit, end_bit);
+    return radix_sort_impl<uint64_t>(h, keys, keys_alt, a, b, false, n, begin_bit, end_bit);
+}
+
+int radix_sort_keys32(Handle &h, uint32_t *&keys, uint32_t *&keys_alt, int64_t n, int begin_bit, int end_bit)
+{
+    unsigned *a = nullptr, *b = nullptr;
+    return radix_sort_impl<uint32_t>(h, keys, keys_alt, a, b, false, n, begin_bit, end_bit);
 }
 
 }  // namespace fmm

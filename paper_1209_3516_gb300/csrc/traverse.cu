@@ -8,7 +8,7 @@
 // takes).  The paper runs the traversal as tasks (TBB / OpenMP 3.0, Sec. 3.3);
 // here it runs in two GPU stages:
 //   1. breadth-first seeding rounds: one thread per (pair, child), until the
-//      frontier holds a few pairs per warp of the device;
+//      frontier holds about four pairs per resident warp of the device;
 //   2. a persistent kernel: each warp claims seeds with an atomic counter and
 //      runs the traversal below each seed depth first on a private stack in
 //      shared memory, four pairs (32 child pairs) per step.  A warp whose stack
@@ -29,6 +29,7 @@ namespace fmm {
 constexpr unsigned kOvM2L = 1u, kOvP2P = 2u, kOvNext = 4u;
 constexpr int kStackCap = 256;      // pairs per warp stack
 constexpr int kStackWarps = 8;      // warps per block of the work-stack kernel
+constexpr int kStackBlocksPerSM = 8;   // 64 resident warps per SM (16 KiB shared memory per block)
 
 struct Cell {
     float4 g;   // centre, radius
@@ -158,27 +159,27 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
 // ---------------------------------------------------------------------------
 // list grouping
 // ---------------------------------------------------------------------------
-__global__ void k_pack_pairs(const int2 *pairs, int64_t n, int cbits, uint64_t *keys)
+template <class K> __global__ void k_pack_pairs(const int2 *pairs, int64_t n, int cbits, K *keys)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 p = pairs[i];
-    keys[i] = ((uint64_t)(unsigned)p.x << cbits) | (uint64_t)(unsigned)p.y;
+    keys[i] = ((K)(unsigned)p.x << cbits) | (K)(unsigned)p.y;
 }
 
-__global__ void k_unpack_sources(const uint64_t *keys, int64_t n, int cbits, int *src)
+template <class K> __global__ void k_unpack_sources(const K *keys, int64_t n, int cbits, int *src)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    src[i] = (int)(keys[i] & ((1ull << cbits) - 1ull));
+    src[i] = (int)(keys[i] & (((K)1 << cbits) - (K)1));
 }
 
 // off[c] = first entry whose target is >= c, for c = 0..ncells.
-__global__ void k_csr_offsets(const uint64_t *keys, int64_t n, int cbits, int ncells, int *off)
+template <class K> __global__ void k_csr_offsets(const K *keys, int64_t n, int cbits, int ncells, int *off)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > ncells) return;
-    const uint64_t v = (uint64_t)c << cbits;
+    const K v = (K)c << cbits;
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -219,29 +220,38 @@ __global__ void k_p2p_pairs(const int2 *pairs, int64_t n, const int *pcnt, unsig
     if (lane_id() == 0 && s) atomicAdd(total, s);
 }
 
-static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
+// Sort the (target, source) pairs by target, then source, packed as
+// target << cbits | source (32-bit keys whenever 2 cbits <= 32), and split
+// them into CSR form: off[c] .. off[c+1] are the sources of target c.
+template <class K> static int group_list_k(Handle &h, const int2 *pairs, int64_t n, int cbits, DevBuf &src, DevBuf &off)
 {
     const int nc = (int)h.ncells;
-    int cbits = 1;
-    while ((1ll << cbits) <= nc) ++cbits;
-    FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(uint64_t)));
-    FMM_TRY(h.lkeys_alt.reserve(std::max<int64_t>(n, 1) * sizeof(uint64_t)));
+    FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(K)));
+    FMM_TRY(h.lkeys_alt.reserve(std::max<int64_t>(n, 1) * sizeof(K)));
     FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
     FMM_TRY(off.reserve((size_t)(nc + 1) * sizeof(int)));
     if (n > 0) {
         ++h.launches;
-        k_pack_pairs<<<ceil_div(n, 256), 256, 0, h.stream>>>(pairs, n, cbits, h.lkeys.as<uint64_t>());
-        uint64_t *k = h.lkeys.as<uint64_t>(), *ka = h.lkeys_alt.as<uint64_t>();
-        FMM_TRY(radix_sort_keys(h, k, ka, n, 0, 2 * cbits));
-        if (k != h.lkeys.as<uint64_t>()) std::swap(h.lkeys, h.lkeys_alt); {
+        k_pack_pairs<K><<<ceil_div(n, 256), 256, 0, h.stream>>>(pairs, n, cbits, h.lkeys.as<K>());
+        K *k = h.lkeys.as<K>(), *ka = h.lkeys_alt.as<K>();
+        if constexpr (sizeof(K) == 4) FMM_TRY(radix_sort_keys32(h, k, ka, n, 0, 2 * cbits));
+        else FMM_TRY(radix_sort_keys(h, k, ka, n, 0, 2 * cbits));
+        if (k != h.lkeys.as<K>()) std::swap(h.lkeys, h.lkeys_alt);
         ++h.launches;
-        k_unpack_sources<<<ceil_div(n, 256), 256, 0, h.stream>>>(h.lkeys.as<uint64_t>(), n, cbits, src.as<int>());
-        }
+        k_unpack_sources<K><<<ceil_div(n, 256), 256, 0, h.stream>>>(h.lkeys.as<K>(), n, cbits, src.as<int>());
     }
     ++h.launches;
-    k_csr_offsets<<<ceil_div(nc + 1, 256), 256, 0, h.stream>>>(h.lkeys.as<uint64_t>(), n, cbits, nc, off.as<int>());
+    k_csr_offsets<K><<<ceil_div(nc + 1, 256), 256, 0, h.stream>>>(h.lkeys.as<K>(), n, cbits, nc, off.as<int>());
     FMM_CHECK_LAUNCH("group list");
     return FMM_OK;
+}
+
+static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
+{
+    int cbits = 1;
+    while ((1ll << cbits) <= h.ncells) ++cbits;
+    if (2 * cbits <= 32) return group_list_k<uint32_t>(h, pairs, n, cbits, src, off);
+    return group_list_k<uint64_t>(h, pairs, n, cbits, src, off);
 }
 
 int build_lists(Handle &h)
@@ -269,7 +279,8 @@ int build_lists(Handle &h)
         h.p2p_cap = (int64_t)nc * 32 + 1024;
         h.front_cap = (int64_t)nc * 8 + 4096;
     }
-    const int seed_target = h.num_sms * 4 * kStackWarps * 8;   // about 8 seeds per resident warp
+    const int stack_blocks = h.num_sms * kStackBlocksPerSM;
+    const int seed_target = stack_blocks * kStackWarps * 4;    // about 4 seeds per resident warp
     for (int attempt = 0;; ++attempt) {
         FMM_TRY(h.m2l_raw.reserve(h.m2l_cap * sizeof(int2)));
         FMM_TRY(h.p2p_raw.reserve(h.p2p_cap * sizeof(int2)));
@@ -328,7 +339,7 @@ int build_lists(Handle &h)
             a.next = h.front[cur ^ 1].as<int2>();
             FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, 2 * sizeof(unsigned long long), h.stream));   // n_next, seed_next
             ++h.launches;
-            k_dtt_stack<<<h.num_sms * 4, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
+            k_dtt_stack<<<stack_blocks, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
             FMM_CHECK_LAUNCH("dtt stack");
             FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));

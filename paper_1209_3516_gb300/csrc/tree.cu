@@ -6,7 +6,7 @@
 //   2. 63-bit keys from 21-bit integer coordinates;
 //   3. stable radix sort of (key, index), gather of FP32 positions;
 //   4. level-by-level split of every cell holding more than ncrit particles
-//      into its non-empty octants (binary searches on the sorted keys);
+//      into its non-empty octants (warp-parallel searches on the sorted keys);
 //   5. cell geometry: geometric centre (exact in FP32) and tight radius
 //      B = max |u_j - X_C| over the cell's particles (Sec. 3.2, B_max MAC),
 //      computed in FP32 with one rounding per operation.
@@ -192,67 +192,74 @@ int build_keys(Handle &h, const double *x)
 // ---------------------------------------------------------------------------
 // 4. ncrit splitting, level by level
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int lower_bound_u64(const uint64_t *keys, int lo, int hi, uint64_t v)
+// First index in [lo, hi) with keys[index] >= v (hi if none), searched by the
+// whole warp: 32 samples per round narrow the range 32-fold, so a cell of a
+// million particles needs 4 dependent rounds instead of 20.  All lanes return
+// the same value.
+__device__ __forceinline__ int warp_lower_bound(const uint64_t *keys, int lo, int hi, uint64_t v)
 {
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (keys[mid] < v) lo = mid + 1;
-        else hi = mid;
+    const int lane = (int)lane_id();
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int p = lo + lane * step;
+        const bool pred = p < hi && keys[p] < v;
+        const int k = __popc(__ballot_sync(kFull, pred));
+        // keys[p_(k-1)] < v <= keys[p_k]: the answer lies in [p_(k-1) + 1, p_k]
+        const int nlo = k == 0 ? lo : lo + (k - 1) * step + 1;
+        const int nhi = min(lo + k * step, hi);
+        lo = nlo;
+        hi = nhi;
     }
-    return lo;
+    const bool pred = lo + lane < hi && keys[lo + lane] < v;
+    return lo + __popc(__ballot_sync(kFull, pred));
 }
 
-// Octant boundaries of cell (level l, prefix p, range [b, e)): bnd[o] = first particle of octant o.
-__device__ __forceinline__ void octant_bounds(const uint64_t *keys, int l, uint64_t p, int b, int e, int *bnd)
+// One warp per cell of level l: the cell splits when it holds more than ncrit
+// particles (and l < 21); its octant boundaries bnd[8 i + o] (first particle of
+// octant o) come from warp searches on the sorted keys, and cnt[i] counts the
+// non-empty octants.
+__global__ void k_split_bounds(int l, int lo, int n, int ncrit, const uint64_t *keys, const uint64_t *prefix,
+                               const int *pbeg, const int *pcnt, int *bnd, unsigned *cnt)
 {
-    const int shift = 3 * (kLevels - (l + 1));
-    bnd[0] = b;
-    bnd[8] = e;
-    int lo = b;
-#pragma unroll
-    for (int o = 1; o < 8; ++o) {
-        lo = lower_bound_u64(keys, lo, e, ((p << 3) | (uint64_t)o) << shift);
-        bnd[o] = lo;
-    }
-}
-
-__global__ void k_split_count(int l, int lo, int n, int ncrit, const uint64_t *keys, const uint64_t *prefix,
-                              const int *pbeg, const int *pcnt, unsigned *cnt)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const int c = lo + i;
+    const int b = pbeg[c], e = b + pcnt[c];
     unsigned nch = 0;
-    if (pcnt[c] > ncrit && l < kLevels) {
-        int bnd[9];
-        octant_bounds(keys, l, prefix[c], pbeg[c], pbeg[c] + pcnt[c], bnd);
-#pragma unroll
-        for (int o = 0; o < 8; ++o) nch += bnd[o + 1] > bnd[o];
+    if (e - b > ncrit && l < kLevels) {
+        const int shift = 3 * (kLevels - (l + 1));
+        const uint64_t p = prefix[c];
+        int prev = b;
+        for (int o = 1; o <= 8; ++o) {
+            const int next = o < 8 ? warp_lower_bound(keys, prev, e, ((p << 3) | (uint64_t)o) << shift) : e;
+            if (lane_id() == 0) bnd[8 * i + o - 1] = prev;
+            nch += next > prev;
+            prev = next;
+        }
     }
-    cnt[i] = nch;
+    if (lane_id() == 0) cnt[i] = nch;
 }
 
-__global__ void k_split_write(int l, int lo, int n, int ncrit, int next_lo, const uint64_t *keys,
-                              const unsigned *off, uint64_t *prefix, int *level, int *pbeg, int *pcnt, int *cbeg,
-                              int *ccnt, int *parent)
+__global__ void k_split_write(int l, int lo, int n, int ncrit, int next_lo, const int *bnd, const unsigned *off,
+                              uint64_t *prefix, int *level, int *pbeg, int *pcnt, int *cbeg, int *ccnt, int *parent)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = lo + i;
+    const int e = pbeg[c] + pcnt[c];
     if (!(pcnt[c] > ncrit && l < kLevels)) return;
-    int bnd[9];
     const uint64_t p = prefix[c];
-    octant_bounds(keys, l, p, pbeg[c], pbeg[c] + pcnt[c], bnd);
     int w = next_lo + (int)off[i];
     cbeg[c] = w;
     int nch = 0;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-        if (bnd[o + 1] > bnd[o]) {
+        const int b0 = bnd[8 * i + o], b1 = o < 7 ? bnd[8 * i + o + 1] : e;
+        if (b1 > b0) {
             prefix[w] = (p << 3) | (uint64_t)o;
             level[w] = l + 1;
-            pbeg[w] = bnd[o];
-            pcnt[w] = bnd[o + 1] - bnd[o];
+            pbeg[w] = b0;
+            pcnt[w] = b1 - b0;
             cbeg[w] = 0;
             ccnt[w] = 0;
             parent[w] = c;
@@ -427,13 +434,14 @@ int build_tree(Handle &h, const double *x)
     for (int l = 0; l < kLevels; ++l) {
         const int64_t lo = h.level_off[l], hi = h.level_off[l + 1], n = hi - lo;
         if (n == 0) break;
-        rc = h.c_tmp.reserve((size_t)(2 * n + 1) * sizeof(unsigned));
+        rc = h.c_tmp.reserve((size_t)(10 * n + 1) * sizeof(unsigned));
         if (rc) break;
         unsigned *cnt = h.c_tmp.as<unsigned>(), *off = cnt + n, *tot = off + n;
+        int *bnd = reinterpret_cast<int *>(tot + 1);
         ++h.launches;
-        k_split_count<<<ceil_div(n, 128), 128, 0, h.stream>>>(l, (int)lo, (int)n, h.ncrit, h.keys.as<uint64_t>(),
-                                                               h.c_prefix.as<uint64_t>(), h.c_pbeg.as<int>(),
-                                                               h.c_pcnt.as<int>(), cnt);
+        k_split_bounds<<<ceil_div(n * 32, 128), 128, 0, h.stream>>>(l, (int)lo, (int)n, h.ncrit, h.keys.as<uint64_t>(),
+                                                                   h.c_prefix.as<uint64_t>(), h.c_pbeg.as<int>(),
+                                                                   h.c_pcnt.as<int>(), bnd, cnt);
         rc = scan_exclusive_u32(h, cnt, off, n, tot);
         if (rc) break;
         cudaError_t e = cudaMemcpyAsync(total_host, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream);
@@ -445,13 +453,11 @@ int build_tree(Handle &h, const double *x)
         const int64_t next = *total_host;
         if (next == 0) break;
         rc = grow_cells(h, hi + next);
-        if (rc) break; {
+        if (rc) break;
         ++h.launches;
         k_split_write<<<ceil_div(n, 128), 128, 0, h.stream>>>(
-            l, (int)lo, (int)n, h.ncrit, (int)hi, h.keys.as<uint64_t>(), off, h.c_prefix.as<uint64_t>(),
-            h.c_level.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
-            h.c_parent.as<int>());
-        }
+            l, (int)lo, (int)n, h.ncrit, (int)hi, bnd, off, h.c_prefix.as<uint64_t>(), h.c_level.as<int>(),
+            h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_parent.as<int>());
         h.level_off.push_back(hi + next);
     }
     if (rc) return rc;
