@@ -95,6 +95,23 @@ def cpu_baseline(a, x, q, reps=1):
             "seconds_per_sample": statistics.median(ts)}
 
 
+def p2p_traffic(a):
+    """DRAM bytes per P2P launch from the committed ncu capture, if it was taken on
+    this workload with the current kernel sources (else None)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_p2p_traffic.json")
+    try:
+        pj = json.load(open(prof))
+        if (pj.get("N"), pj.get("P"), pj.get("theta"), pj.get("ncrit")) != (a.N, a.P, a.theta, a.ncrit):
+            return None
+        h = hashlib.sha256()
+        for f in pj["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return pj["dram_bytes_per_launch"] if h.hexdigest() == pj["sources_sha256"] else None
+    except Exception:
+        return None
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -287,15 +304,7 @@ def run_ours(a):
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = pairs * FLOPS_PER_PAIR / (p2p_mean * 1e-3) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "p2p_traffic.json")
-    if os.path.exists(prof):
-        try:
-            pj = json.load(open(prof))
-            if pj.get("N") == a.N and pj.get("P") == a.P and pj.get("theta") == a.theta and pj.get("ncrit") == a.ncrit:
-                traffic = pj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = p2p_traffic(a)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

@@ -9,8 +9,8 @@
 //
 // Kernel layout:
 //   P2M  one warp per leaf, lanes over its particles, warp reduction;
-//   M2M  one thread per cell of a level (P <= 6) or one warp per cell over a
-//        term table (P = 8), summing its children (bottom-up);
+//   M2M  one thread per cell of a level (P <= 6) or one warp per cell with
+//        three one-dimensional shifts (P = 8), summing its children (bottom-up);
 //   M2L  one warp per target cell, lanes over its M2L sources, each lane
 //        computing the kernel derivatives D_m(R) of its pair and contracting,
 //        then a warp reduction of the T local coefficients;
@@ -33,6 +33,37 @@ template <int T> __device__ __forceinline__ void warp_reduce_vec(float *v)
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int i = 0; i < T; ++i) v[i] += __shfl_xor_sync(kFull, v[i], o);
+}
+
+template <int N> struct Pad32Pow2 {   // smallest 32 * 2^j >= N
+    static constexpr int value = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+};
+template <int N> struct ScatterLen {  // array length warp_reduce_scatter<N> needs
+    static constexpr int value = N > Pad32Pow2<N>::value / 2 ? N : Pad32Pow2<N>::value / 2;
+};
+
+// Sum N values across the warp by recursive halving over V = Pad32Pow2<N>
+// slots (slots >= N are zero): on return lane l holds the sums of slots
+// [K l, K l + K) in v[0..K), K = V / 32.  Costs about V shuffles instead of
+// 5 N for a butterfly on every value.  v must hold ScatterLen<N> floats.
+template <int N> __device__ __forceinline__ void warp_reduce_scatter(float *v)
+{
+    constexpr int V = Pad32Pow2<N>::value;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int half = V >> (step + 1);
+        const unsigned mask = 16u >> step;
+        const bool upper = (lane & mask) != 0u;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float lo = (step > 0 || i < N) ? v[i] : 0.0f;
+            const float hi = (step > 0 || i + half < N) ? v[i + half] : 0.0f;
+            const float send = upper ? lo : hi;
+            const float keep = upper ? hi : lo;
+            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+    }
 }
 
 // Write a T-vector (held by every lane) to dst[0..TP), lanes striding.
@@ -61,9 +92,9 @@ __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const 
     const int fr = parent[c] >= 0 ? parent[c] : c;
     const float4 Xc = geom[c], Xf = geom[fr];
     const float ox = (Xc.x - Xf.x) * inv_s, oy = (Xc.y - Xf.y) * inv_s, oz = (Xc.z - Xf.z) * inv_s;
-    float acc[T];
+    float acc[ScatterLen<T>::value];
 #pragma unroll
-    for (int i = 0; i < T; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < ScatterLen<T>::value; ++i) acc[i] = 0.0f;
     const int b = pbeg[c], e = b + pcnt[c];
     for (int j = b + (int)lane_id(); j < e; j += 32) {
         const float4 p = pos[j];
@@ -72,8 +103,18 @@ __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const 
 #pragma unroll
         for (int i = 0; i < T; ++i) acc[i] = fmaf(p.w, w[i], acc[i]);
     }
-    warp_reduce_vec<T>(acc);
-    warp_store_vec<T, TP>(acc, M + (size_t)c * TP);
+    if constexpr (T <= 64) {
+        constexpr int K = Pad32Pow2<T>::value / 32;
+        warp_reduce_scatter<T>(acc);
+        float *dst = M + (size_t)c * TP;
+        const int lane = (int)lane_id();
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (K * lane + j < TP) dst[K * lane + j] = K * lane + j < T ? acc[j] : 0.0f;
+    } else {
+        warp_reduce_vec<T>(acc);
+        warp_store_vec<T, TP>(acc, M + (size_t)c * TP);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -128,97 +169,129 @@ __global__ void k_m2m(int lo, int n, const int *cbeg, const int *ccnt, const flo
     for (int t = 0; t < TP; ++t) dst[t] = t < T ? acc[t] : 0.0f;
 }
 
-// Higher orders: one warp per cell, lanes over the terms (k, m) of the shift
-// from a term table.  With s the child's octant signs, the factor of a term is
-// 2^-|k| prod_i (-s_i)^(j_i) / j_i!, j = k - m: the table holds k, m, the parity
-// of j per axis and 1/j!; the sign and 2^-|k| are applied here.  The table is
-// ordered m-major, so the 32 lanes of a step add into distinct outputs k of a
-// shared-memory accumulator.
-struct M2MTerm {
-    unsigned kmp;   // k | m << 8 | (j_x odd, j_y odd, j_z odd) << 16
-    float coef;     // 1 / (j_x! j_y! j_z!)
-};
+// Storage index of (a, b, c) and its inverse (degree-graded order of mi.cuh).
+__device__ __forceinline__ int mi_index(int a, int b, int c)
+{
+    const int n = a + b + c, bc = b + c;
+    return n * (n + 1) * (n + 2) / 6 + bc * (bc + 1) / 2 + c;
+}
 
+__device__ __forceinline__ void mi_decode(int i, int &a, int &b, int &c)
+{
+    int n = 0;
+    while ((n + 1) * (n + 2) * (n + 3) / 6 <= i) ++n;
+    const int r = i - n * (n + 1) * (n + 2) / 6;   // position inside degree n
+    int bc = 0;                                    // b + c = n - a
+    while ((bc + 1) * (bc + 2) / 2 <= r) ++bc;
+    c = r - bc * (bc + 1) / 2;
+    b = bc - c;
+    a = n - bc;
+}
+
+// Higher orders: the shift is separable.  With s the child's octant signs,
+//   Mb_k(P) = 2^-|k| sum_{m <= k} Mb_m(C) prod_i (-s_i)^(k_i - m_i) / (k_i - m_i)!,
+// i.e. three one-dimensional shifts (along x, then y, then z), each
+//   A_k = sum_{j = 0..k_i} B_{k - j e_i} (-s_i)^j / j!,
+// which read only lower indices of the same truncated set.  One warp per
+// parent cell, lanes over the output coefficients, the intermediate arrays
+// in shared memory.
 template <int P>
-__global__ void __launch_bounds__(128) k_m2m_table(int lo, int n, const int *cbeg, const int *ccnt,
-                                                   const float4 *geom, const M2MTerm *terms, int nterms, float *M)
+__global__ void __launch_bounds__(128) k_m2m_sep(int lo, int n, const int *cbeg, const int *ccnt,
+                                                 const float4 *geom, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
-    __shared__ float acc_s[4][TP];
+    constexpr int KPL = (T + 31) / 32;   // outputs per lane
+    __shared__ float buf_s[4][2][TP];
     const int w = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = (int)lane_id();
     if (i >= n) return;
     const int c = lo + i;
     const int nch = ccnt[c];
-    if (nch == 0) return;
-    float *acc = acc_s[w];
-    for (int k = lane; k < TP; k += 32) acc[k] = 0.0f;
-    __syncwarp();
+    if (nch == 0) return;   // leaf: its multipole comes from P2M
+    float *b0 = buf_s[w][0], *b1 = buf_s[w][1];
+    int ka[KPL], kb[KPL], kc[KPL];
+    float acc[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+        acc[j] = 0.0f;
+        const int k = lane + 32 * j;
+        if (k < T) mi_decode(k, ka[j], kb[j], kc[j]);
+        else ka[j] = kb[j] = kc[j] = 0;
+    }
     const float4 Xp = geom[c];
     for (int q = 0; q < nch; ++q) {
         const int ch = cbeg[c] + q;
         const float4 Xc = geom[ch];
-        const unsigned flip = (Xc.x > Xp.x ? 1u : 0u) | (Xc.y > Xp.y ? 2u : 0u) | (Xc.z > Xp.z ? 4u : 0u);
+        // factor per axis: (-s_i)^j / j!, -s_i = -1 when the child lies above the parent centre
+        const float sx = Xc.x > Xp.x ? -1.0f : 1.0f, sy = Xc.y > Xp.y ? -1.0f : 1.0f,
+                    sz = Xc.z > Xp.z ? -1.0f : 1.0f;
         const float *mc = M + (size_t)ch * TP;
-        for (int t = lane; t < nterms; t += 32) {
-            const M2MTerm e = terms[t];
-            const unsigned k = e.kmp & 0xffu, m = (e.kmp >> 8) & 0xffu, par = e.kmp >> 16;
-            const float v = __ldg(mc + m) * ((__popc(par & flip) & 1) ? -e.coef : e.coef);
-            atomicAdd(acc + k, v);
-        }
-    }
-    __syncwarp();
-    float *dst = M + (size_t)c * TP;
-    for (int k = lane; k < TP; k += 32) {
-        if (k < T) {
-            int n_deg = 0;
-            while ((n_deg + 1) * (n_deg + 2) * (n_deg + 3) / 6 <= k) ++n_deg;
-            dst[k] = ldexpf(acc[k], -n_deg);
-        } else {
-            dst[k] = 0.0f;
-        }
-    }
-}
-
-// Host: the term table of order P, m-major.
-static std::vector<M2MTerm> m2m_term_table(int P)
-{
-    auto idx = [](int a, int b, int c) {
-        const int n = a + b + c, bc = b + c;
-        return n * (n + 1) * (n + 2) / 6 + bc * (bc + 1) / 2 + c;
-    };
-    double fact[16];
-    fact[0] = 1.0;
-    for (int i = 1; i < 16; ++i) fact[i] = fact[i - 1] * i;
-    std::vector<M2MTerm> out;
-    for (int mn = 0; mn < P; ++mn)
-        for (int ma = mn; ma >= 0; --ma)
-            for (int mb = mn - ma; mb >= 0; --mb) {
-                const int mc = mn - ma - mb;
-                for (int kn = mn; kn < P; ++kn)
-                    for (int ka = kn; ka >= 0; --ka)
-                        for (int kb = kn - ka; kb >= 0; --kb) {
-                            const int kc = kn - ka - kb;
-                            if (ka < ma || kb < mb || kc < mc) continue;
-                            const int ja = ka - ma, jb = kb - mb, jc = kc - mc;
-                            M2MTerm e;
-                            e.kmp = (unsigned)idx(ka, kb, kc) | ((unsigned)idx(ma, mb, mc) << 8) |
-                                    ((unsigned)((ja & 1) | ((jb & 1) << 1) | ((jc & 1) << 2)) << 16);
-                            e.coef = (float)(1.0 / (fact[ja] * fact[jb] * fact[jc]));
-                            out.push_back(e);
-                        }
+        for (int k = lane; k < T; k += 32) b0[k] = mc[k];
+        __syncwarp();
+        float t[KPL];
+        // x shift: b0 -> b1
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) {
+            t[j] = 0.0f;
+            if (lane + 32 * j >= T) continue;
+            float f = 1.0f;
+            for (int d = 0; d <= ka[j]; ++d) {
+                t[j] = fmaf(b0[mi_index(ka[j] - d, kb[j], kc[j])], f, t[j]);
+                f *= sx / (float)(d + 1);
             }
-    return out;
+        }
+#pragma unroll
+        for (int j = 0; j < KPL; ++j)
+            if (lane + 32 * j < T) b1[lane + 32 * j] = t[j];
+        __syncwarp();
+        // y shift: b1 -> b0 (b0 is no longer read by anyone)
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) {
+            t[j] = 0.0f;
+            if (lane + 32 * j >= T) continue;
+            float f = 1.0f;
+            for (int d = 0; d <= kb[j]; ++d) {
+                t[j] = fmaf(b1[mi_index(ka[j], kb[j] - d, kc[j])], f, t[j]);
+                f *= sy / (float)(d + 1);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < KPL; ++j)
+            if (lane + 32 * j < T) b0[lane + 32 * j] = t[j];
+        __syncwarp();
+        // z shift, accumulated over the children
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) {
+            if (lane + 32 * j >= T) continue;
+            float s = 0.0f, f = 1.0f;
+            for (int d = 0; d <= kc[j]; ++d) {
+                s = fmaf(b0[mi_index(ka[j], kb[j], kc[j] - d)], f, s);
+                f *= sz / (float)(d + 1);
+            }
+            acc[j] += s;
+        }
+        __syncwarp();   // b0 is refilled by the next child
+    }
+    float *dst = M + (size_t)c * TP;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+        const int k = lane + 32 * j;
+        if (k < T) dst[k] = ldexpf(acc[j], -(ka[j] + kb[j] + kc[j]));
+    }
+    for (int k = T + lane; k < TP; k += 32) dst[k] = 0.0f;
 }
 
 // ---------------------------------------------------------------------------
 // M2L: Lb_n(T) = (1/s_T) sum_S sum_k (s_S/s_T)^|k| Mb_k(S) D_{n+k}((X_T - X_S)/s_T)
 // One warp per target cell, lanes over its M2L sources; each lane computes the
 // kernel derivatives of its pair and contracts them with the source multipole
-// into the output coefficients N0 <= idx(n) < N1 (all of them for P <= 6; for
-// P = 8 two passes over the sources, each recomputing D, keep everything in
-// registers), then the warp sums its lanes.
+// (streamed from memory as float4) into the output coefficients
+// N0 <= idx(n) < N1, then the warp sums its lanes.  A single pass over all
+// outputs is used: splitting the outputs over two passes (recomputing D) keeps
+// P = 8 spill-free but doubles the unrolled code and loses to instruction-cache
+// misses (measured 1.26 ms vs 0.76 ms at N = 1M, theta = 0.5).
 // ---------------------------------------------------------------------------
 template <int P, int N0, int N1>
 __device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, const int *level, const float4 *geom,
@@ -228,9 +301,9 @@ __device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, 
     const float4 Xt = geom[t];
     const int lt = level[t];
     const float inv_st = ldexpf(1.0f, lt);
-    float acc[NO];
+    float acc[ScatterLen<NO>::value];
 #pragma unroll
-    for (int i = 0; i < NO; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < ScatterLen<NO>::value; ++i) acc[i] = 0.0f;
     const int b = off[t], e = off[t + 1];
     for (int k = b + (int)lane_id(); k < e; k += 32) {
         const int s = src[k];
@@ -244,15 +317,22 @@ __device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, 
         for (int d = 1; d < P; ++d) rho_pow[d] = rho_pow[d - 1] * rho;
         m2l_contract_range<P, N0, N1>(reinterpret_cast<const float4 *>(M + (size_t)s * TP), rho_pow, D, acc);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < NO; ++i) acc[i] += __shfl_xor_sync(kFull, acc[i], o);
     float *dst = L + (size_t)t * TP;
     const int lane = (int)lane_id();
+    if constexpr (NO <= 64) {
+        constexpr int K = Pad32Pow2<NO>::value / 32;
+        warp_reduce_scatter<NO>(acc);
 #pragma unroll
-    for (int i = 0; i < NO; ++i)
-        if ((i & 31) == lane) dst[N0 + i] = acc[i] * inv_st;
+        for (int j = 0; j < K; ++j) {
+            const int i = K * lane + j;
+            if (i < NO) dst[N0 + i] = acc[j] * inv_st;
+        }
+    } else {
+        warp_reduce_vec<NO>(acc);
+#pragma unroll
+        for (int i = 0; i < NO; ++i)
+            if ((i & 31) == lane) dst[N0 + i] = acc[i] * inv_st;
+    }
     if (N1 == T)
         for (int i = T + lane; i < TP; i += 32) dst[i] = 0.0f;
 }
@@ -264,13 +344,7 @@ __global__ void __launch_bounds__(128) k_m2l(int ncells, const int *off, const i
     constexpr int T = MI<P>::T;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= ncells) return;
-    if constexpr (P >= 8) {
-        constexpr int split = MI<P>::idx(5, 0, 0);   // outputs of degree <= 4 | degree >= 5
-        m2l_pass<P, 0, split>(t, off, src, level, geom, M, L);
-        m2l_pass<P, split, T>(t, off, src, level, geom, M, L);
-    } else {
-        m2l_pass<P, 0, T>(t, off, src, level, geom, M, L);
-    }
+    m2l_pass<P, 0, T>(t, off, src, level, geom, M, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -333,20 +407,12 @@ template <int P> static int upward_impl(Handle &h, const float *q)
                                                                     h.c_pcnt.as<int>(), h.c_level.as<int>(),
                                                                     h.c_parent.as<int>(), h.c_geom.as<float4>(),
                                                                     h.pos.as<float4>(), h.M.as<float>());
-    if (P >= 8 && h.m2m_nterms == 0) {
-        const std::vector<M2MTerm> tab = m2m_term_table(P);
-        FMM_TRY(h.m2m_terms.reserve(tab.size() * sizeof(M2MTerm)));
-        FMM_CUDA(cudaMemcpy(h.m2m_terms.p, tab.data(), tab.size() * sizeof(M2MTerm), cudaMemcpyHostToDevice));
-        h.m2m_nterms = (int)tab.size();
-    }
-    const int nterms = h.m2m_nterms;
     for (int l = h.nlevels - 2; l >= 0; --l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
         ++h.launches;
         if (P >= 8)
-            k_m2m_table<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
-                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), h.m2m_terms.as<M2MTerm>(),
-                nterms, h.M.as<float>());
+            k_m2m_sep<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
+                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), h.M.as<float>());
         else
             k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
                                                            h.c_geom.as<float4>(), h.M.as<float>());

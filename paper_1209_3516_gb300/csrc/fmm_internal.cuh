@@ -71,6 +71,7 @@ struct TravCounters {
     unsigned long long p2p_pairs; // sum over P2P pairs of n_target * n_source
     unsigned int overflow;        // bit 0: m2l, bit 1: p2p, bit 2: frontier/spill
     unsigned int nleaves;         // leaves found by the leaf-list kernel
+    unsigned long long round_count[16];   // frontier size before each seeding round
 };
 
 // Page-locked host scratch of a handle (counters read back during a build).
@@ -144,8 +145,7 @@ struct Handle {
 
     // expansions and outputs
     DevBuf M, L;          // float[ncells * TP]
-    DevBuf m2m_terms;     // term table of the high-order M2M kernel
-    int m2m_nterms = 0;
+
     DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
     DevBuf energy_part;   // double partials
 

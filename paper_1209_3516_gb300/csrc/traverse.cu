@@ -92,9 +92,14 @@ __device__ __forceinline__ bool child_pair(const TravArgs &a, int2 pr, int j, in
     return true;
 }
 
-// Seeding round: one thread per (frontier pair, child slot).
-__global__ void k_dtt_round(const int2 *front, unsigned long long nfront, TravArgs a)
+// Seeding round: one thread per (frontier pair, child slot).  The frontier size
+// is read from device memory (*nfront_p, at most the buffer capacity), the next
+// frontier's size is counted into *nnext_p, so rounds run back to back without
+// the host.
+__global__ void k_dtt_round(const int2 *front, const unsigned long long *nfront_p, unsigned long long *nnext_p,
+                            TravArgs a)
 {
+    const unsigned long long nfront = min(*nfront_p, a.next_cap);
     const unsigned long long total = nfront * 8ull;
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -108,14 +113,15 @@ __global__ void k_dtt_round(const int2 *front, unsigned long long nfront, TravAr
         }
         warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
         warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
-        warp_append(kind == 3, np, a.next, a.next_cap, &a.ctr->n_next, &a.ctr->overflow, kOvNext);
+        warp_append(kind == 3, np, a.next, a.next_cap, nnext_p, &a.ctr->overflow, kOvNext);
     }
 }
 
-// Persistent work-stack kernel.
-__global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seeds, unsigned long long nseeds,
+// Persistent work-stack kernel; the seed count is read from device memory.
+__global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seeds, const unsigned long long *nseeds_p,
                                                                 TravArgs a)
 {
+    const unsigned long long nseeds = min(*nseeds_p, a.next_cap);
     __shared__ int2 stack[kStackWarps][kStackCap];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     int2 *st = stack[w];
@@ -280,13 +286,20 @@ int build_lists(Handle &h)
         h.front_cap = (int64_t)nc * 8 + 4096;
     }
     const int stack_blocks = h.num_sms * kStackBlocksPerSM;
-    const int seed_target = stack_blocks * kStackWarps * 4;    // about 4 seeds per resident warp
+    // seeding rounds: each splits one side of every frontier pair, so the frontier
+    // grows by at most 8x per round; enough rounds for ~4 seeds per resident warp
+    const int64_t seed_target = (int64_t)stack_blocks * kStackWarps * 4;
+    int nrounds = 0;
+    for (int64_t f = 1; f < seed_target && nrounds < 2 * h.nlevels && nrounds < 15; f *= 8) ++nrounds;
+    const int round_blocks = h.num_sms * 16;
     for (int attempt = 0;; ++attempt) {
         FMM_TRY(h.m2l_raw.reserve(h.m2l_cap * sizeof(int2)));
         FMM_TRY(h.p2p_raw.reserve(h.p2p_cap * sizeof(int2)));
         FMM_TRY(h.front[0].reserve(h.front_cap * sizeof(int2)));
         FMM_TRY(h.front[1].reserve(h.front_cap * sizeof(int2)));
+        // zero the counters, keeping the leaf count found above
         FMM_CUDA(cudaMemsetAsync(ctr, 0, offsetof(TravCounters, nleaves), h.stream));
+        FMM_CUDA(cudaMemsetAsync(&ctr->round_count[0], 0, sizeof(ctr->round_count), h.stream));
         TravArgs a;
         a.geom = h.c_geom.as<float4>();
         a.kids = h.c_kids.as<int2>();
@@ -297,18 +310,8 @@ int build_lists(Handle &h)
         a.p2p_cap = h.p2p_cap;
         a.next_cap = h.front_cap;
         a.ctr = ctr;
-        int cur = 0;
-        unsigned long long nfront = 0;
-        bool overflow = false;
-        // the root pair (a root leaf is its own single P2P pair)
-        {
-            int2 root = make_int2(0, 0);
-            FMM_CUDA(cudaMemcpyAsync(h.front[0].p, &root, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
-            FMM_CUDA(cudaMemcpyAsync(&h.pinned->root_kids, h.c_kids.p, sizeof(int2), cudaMemcpyDeviceToHost,
-                                     h.stream));
-            FMM_CUDA(cudaStreamSynchronize(h.stream));
-        }
-        if (h.pinned->root_kids.y == 0) {
+        if (h.nlevels <= 1) {
+            // the root is a leaf: the single P2P pair (root, root)
             int2 rp = make_int2(0, 0);
             FMM_CUDA(cudaMemcpyAsync(h.p2p_raw.p, &rp, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));
@@ -316,30 +319,31 @@ int build_lists(Handle &h)
             h.n_p2p = 1;
             break;
         }
-        nfront = 1;
-        // 1. seeding rounds
-        while (nfront > 0 && nfront < (unsigned long long)seed_target) {
+        // the pair (root, root) seeds round 0
+        h.pinned->ctr = TravCounters();
+        h.pinned->ctr.round_count[0] = 1;
+        int2 root = make_int2(0, 0);
+        FMM_CUDA(cudaMemcpyAsync(h.front[0].p, &root, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
+        FMM_CUDA(cudaMemcpyAsync(&ctr->round_count[0], &h.pinned->ctr.round_count[0], sizeof(unsigned long long),
+                                 cudaMemcpyHostToDevice, h.stream));
+        // 1. seeding rounds, back to back
+        int cur = 0;
+        for (int r = 0; r < nrounds; ++r) {
             a.next = h.front[cur ^ 1].as<int2>();
-            FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, sizeof(unsigned long long), h.stream));
-            const int blocks = (int)std::min<unsigned long long>((nfront * 8 + 255) / 256, (unsigned long long)h.num_sms * 16);
             ++h.launches;
-            k_dtt_round<<<blocks, 256, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
-            FMM_CHECK_LAUNCH("dtt round");
-            FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
-            FMM_CUDA(cudaStreamSynchronize(h.stream));
-            if (hc->overflow) {
-                overflow = true;
-                break;
-            }
-            nfront = hc->n_next;
+            k_dtt_round<<<round_blocks, 256, 0, h.stream>>>(h.front[cur].as<int2>(), &ctr->round_count[r],
+                                                            &ctr->round_count[r + 1], a);
             cur ^= 1;
         }
-        // 2. work-stack kernel, relaunched on spilled pairs
-        while (!overflow && nfront > 0) {
+        FMM_CHECK_LAUNCH("dtt rounds");
+        // 2. work-stack kernel on the last frontier, relaunched on spilled pairs
+        const unsigned long long *nseeds_dev = &ctr->round_count[nrounds];
+        bool overflow = false;
+        for (;;) {
             a.next = h.front[cur ^ 1].as<int2>();
             FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, 2 * sizeof(unsigned long long), h.stream));   // n_next, seed_next
             ++h.launches;
-            k_dtt_stack<<<stack_blocks, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nfront, a);
+            k_dtt_stack<<<stack_blocks, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nseeds_dev, a);
             FMM_CHECK_LAUNCH("dtt stack");
             FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));
@@ -347,7 +351,12 @@ int build_lists(Handle &h)
                 overflow = true;
                 break;
             }
-            nfront = hc->n_next;
+            if (hc->n_next == 0) break;
+            nseeds_dev = &ctr->n_next;   // the spilled pairs seed the next launch
+            // the seed count must survive the reset of n_next: keep it in the last round slot
+            FMM_CUDA(cudaMemcpyAsync(&ctr->round_count[15], &ctr->n_next, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToDevice, h.stream));
+            nseeds_dev = &ctr->round_count[15];
             cur ^= 1;
         }
         if (!overflow) {
@@ -366,9 +375,11 @@ int build_lists(Handle &h)
         }
         // The traversal stopped at the first overflow, so the counters are lower
         // bounds: at least double what overflowed and run again.
+        unsigned long long max_round = hc->n_next;
+        for (int r = 0; r <= nrounds; ++r) max_round = std::max(max_round, hc->round_count[r]);
         if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 3 / 2) + 1024);
         if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 3 / 2) + 1024);
-        if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 2, (int64_t)(hc->n_next * 3 / 2) + 4096);
+        if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 2, (int64_t)(max_round * 3 / 2) + 4096);
     }
     phase_end(h, FMM_PHASE_TRAVERSE);
 
