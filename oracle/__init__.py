@@ -54,6 +54,12 @@ def lib():
             L.orc_l2p.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp, _dp]
             L.orc_l2p.restype = ctypes.c_int
             L.orc_direct.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_int64, _i64p, _dp, _dp]
+            L.orc_direct_backward.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int64, _i64p,
+                                              _dp, _dp]
+            L.orc_p2m_dipole.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.orc_p2m_dipole.restype = ctypes.c_int
+            L.orc_l2p_hess.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.orc_l2p_hess.restype = ctypes.c_int
             L.orc_morton.argtypes = [ctypes.c_uint32] * 3
             L.orc_morton.restype = ctypes.c_uint64
             L.orc_create.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_int]
@@ -63,6 +69,8 @@ def lib():
             L.orc_build.restype = ctypes.c_int
             L.orc_evaluate.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p, _dp, _dp]
             L.orc_evaluate.restype = ctypes.c_int
+            L.orc_backward.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int64, _i64p, _dp, _dp]
+            L.orc_backward.restype = ctypes.c_int
             for name in ("orc_ncells", "orc_nm2l", "orc_np2p"):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
                 getattr(L, name).restype = ctypes.c_int64
@@ -156,6 +164,25 @@ def l2p(P, L, Xt, x):
     return phi, grad
 
 
+def p2m_dipole(P, y, a, p, X):
+    """Multipole of sources with charges a and dipoles p (n x 3) about X."""
+    y = _f64(y, (-1, 3))
+    a = _f64(a, (-1,))
+    p = _f64(p, (-1, 3))
+    M = np.zeros(nterms(P))
+    assert lib().orc_p2m_dipole(P, y.shape[0], _ptr(y, _dp), _ptr(a, _dp), _ptr(p, _dp),
+                                _ptr(_f64(X, (3,)), _dp), _ptr(M, _dp)) == 0
+    return M
+
+
+def l2p_hess(P, L, Xt, x, v):
+    """Hessian of the local expansion L (about Xt) at x, applied to v."""
+    hv = np.zeros(3)
+    assert lib().orc_l2p_hess(P, _ptr(_f64(L), _dp), _ptr(_f64(Xt, (3,)), _dp), _ptr(_f64(x, (3,)), _dp),
+                              _ptr(_f64(v, (3,)), _dp), _ptr(hv, _dp)) == 0
+    return hv
+
+
 def morton(ix: int, iy: int, iz: int) -> int:
     return int(lib().orc_morton(ix, iy, iz))
 
@@ -175,6 +202,25 @@ def direct(x, q, targets=None):
     lib().orc_direct(N, _ptr(x, _dp), _ptr(q, _dp), nt if tp is not None else 0,
                      _ptr(tp, _i64p), _ptr(phi, _dp), _ptr(grad, _dp))
     return phi, grad
+
+
+def direct_backward(x, q, dphi=None, dgrad=None, targets=None):
+    """FP64 adjoint of the direct sum: (dL/dq, dL/dx) for upstream dL/dphi, dL/dgrad."""
+    x = _f64(x, (-1, 3))
+    q = _f64(q, (-1,))
+    N = x.shape[0]
+    a = None if dphi is None else _f64(dphi, (N,))
+    b = None if dgrad is None else _f64(dgrad, (N, 3))
+    if targets is None:
+        nt, tp = N, None
+    else:
+        tp = np.ascontiguousarray(targets, dtype=np.int64)
+        nt = tp.shape[0]
+    dq = np.zeros(nt)
+    dx = np.zeros((nt, 3))
+    lib().orc_direct_backward(N, _ptr(x, _dp), _ptr(q, _dp), _ptr(a, _dp), _ptr(b, _dp),
+                              nt if tp is not None else 0, _ptr(tp, _i64p), _ptr(dq, _dp), _ptr(dx, _dp))
+    return dq, dx
 
 
 class FMM:
@@ -213,6 +259,24 @@ class FMM:
         if rc != 0:
             raise ValueError("oracle evaluate failed")
         return phi, grad
+
+    def backward(self, q, dphi=None, dgrad=None, targets=None):
+        """FMM adjoint: (dL/dq, dL/dx) for charges q and upstream dL/dphi, dL/dgrad."""
+        q = _f64(q, (self.N,))
+        a = None if dphi is None else _f64(dphi, (self.N,))
+        b = None if dgrad is None else _f64(dgrad, (self.N, 3))
+        if targets is None:
+            nt, tp = self.N, None
+        else:
+            tp = np.ascontiguousarray(targets, dtype=np.int64)
+            nt = tp.shape[0]
+        dq = np.zeros(nt)
+        dx = np.zeros((nt, 3))
+        rc = lib().orc_backward(self._h, _ptr(q, _dp), _ptr(a, _dp), _ptr(b, _dp), nt if tp is not None else 0,
+                                _ptr(tp, _i64p), _ptr(dq, _dp), _ptr(dx, _dp))
+        if rc != 0:
+            raise ValueError("oracle backward failed")
+        return dq, dx
 
     @property
     def ncells(self) -> int:

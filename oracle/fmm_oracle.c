@@ -37,6 +37,16 @@
  * Readings of points the paper leaves open (normalisation constants, the
  * split tie-break, the degree convention, coincident points) are stated at
  * the function that takes them.
+ *
+ * Adjoint (not in the paper: the derivatives of the sums above).  For a
+ * scalar loss with upstream gradients a_i = dL/dphi_i and b_i = dL/dgrad_i,
+ *   dq_k = Psi(x_k),  Psi(x) = sum_i a_i G(x - x_i) + sum_i b_i . grad_y G(x - y)|_{y = x_i}
+ *   dx_k = a_k grad_k + H(x_k) b_k + q_k grad Psi(x_k),
+ * with G = 1/r and H the Hessian of phi: Psi is the field of charges a and
+ * dipoles b, so the same traversal lists, the same translation operators and a
+ * dipole P2M give it; H b needs the second derivatives of the local expansion
+ * of phi and of the P2P kernel.  orc_direct_backward is the plain definition
+ * (O(N^2)); orc_backward takes these FMM steps.
  */
 #include <math.h>
 #include <stdint.h>
@@ -307,6 +317,55 @@ static void orc_l2p_mi(const orc_mindex *mi, const double *L, const double *Xt, 
     }
 }
 
+/*
+ * Dipole P2M: the multipole of a dipole p at y is p . grad_y of the multipole
+ * of a unit charge at y: d/dy_c (d^k / k!) = d^(k - e_c) / (k - e_c)!, so
+ *   M_k(C) += a_j d_j^k / k! + sum_c p_{j,c} d_j^(k - e_c) / (k - e_c)!,  d_j = y_j - X_C,
+ * for sources carrying a charge a_j and a dipole p_j (3 per source).
+ */
+static void orc_p2m_dipole_mi(const orc_mindex *mi, int n, const double *y, const double *a,
+                              const double *p, const double *X, double *M)
+{
+    for (int j = 0; j < n; ++j) {
+        double d[3] = {y[3 * j] - X[0], y[3 * j + 1] - X[1], y[3 * j + 2] - X[2]};
+        for (int t = 0; t < mi->nterms; ++t) {
+            const int *k = mi->k[t];
+            M[t] += a[j] * orc_mpow(d, k) / orc_mfact(k);
+            for (int c = 0; c < 3; ++c) {
+                if (k[c] == 0) continue;
+                int km[3] = {k[0], k[1], k[2]};
+                km[c] -= 1;
+                M[t] += p[3 * j + c] * orc_mpow(d, km) / orc_mfact(km);
+            }
+        }
+    }
+}
+
+/*
+ * Hessian-vector product of a local expansion: hv_a += sum_b v_b d^2/dx_a dx_b
+ * sum_n L_n r^n, r = x - X_T, for one point x and one vector v.
+ */
+static void orc_l2p_hess_mi(const orc_mindex *mi, const double *L, const double *Xt,
+                            const double *x, const double *v, double *hv)
+{
+    double r[3] = {x[0] - Xt[0], x[1] - Xt[1], x[2] - Xt[2]};
+    for (int t = 0; t < mi->nterms; ++t) {
+        const int *k = mi->k[t];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                /* d/dx_b d/dx_a r^k: factor k_a (k_b - [a == b]) times r^(k - e_a - e_b) */
+                int km[3] = {k[0], k[1], k[2]};
+                double f = km[a];
+                km[a] -= 1;
+                if (f == 0.0) continue;
+                f *= km[b];
+                km[b] -= 1;
+                if (f == 0.0) continue;
+                hv[a] += L[t] * f * orc_mpow(r, km) * v[b];
+            }
+    }
+}
+
 /* Stand-alone operator entry points (arrays in the oracle's multi-index order). */
 static orc_mindex *orc_mindex_new(int P)
 {
@@ -371,6 +430,25 @@ int orc_l2p(int P, const double *L, const double *Xt, int n, const double *x, do
     return 0;
 }
 
+int orc_p2m_dipole(int P, int n, const double *y, const double *a, const double *p, const double *X,
+                   double *M)
+{
+    orc_mindex *mi = orc_mindex_new(P);
+    if (!mi) return -1;
+    orc_p2m_dipole_mi(mi, n, y, a, p, X, M);
+    orc_mindex_delete(mi);
+    return 0;
+}
+
+int orc_l2p_hess(int P, const double *L, const double *Xt, const double *x, const double *v, double *hv)
+{
+    orc_mindex *mi = orc_mindex_new(P);
+    if (!mi) return -1;
+    orc_l2p_hess_mi(mi, L, Xt, x, v, hv);
+    orc_mindex_delete(mi);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Direct O(N^2) sum: the plain definition the FMM approximates.       */
 /* ------------------------------------------------------------------ */
@@ -407,6 +485,59 @@ void orc_direct(int64_t N, const double *x, const double *q, int64_t nt, const i
         grad[3 * t] = gx;
         grad[3 * t + 1] = gy;
         grad[3 * t + 2] = gz;
+    }
+}
+
+/*
+ * Adjoint of the direct sum, written out from the definition.  With
+ * phi_i = sum_{j != i} q_j / r_ij and grad_i = -sum_{j != i} q_j d_ij / r_ij^3
+ * (d_ij = x_i - x_j), and upstream gradients a_i (potential) and b_i
+ * (gradient, 3 per particle) of a scalar loss L:
+ *   dL/dq_k = sum_{i != k} [ a_i / r_ik - b_i . d_ik / r_ik^3 ]
+ *   dL/dx_k = a_k grad_k + sum_{i != k} a_i q_k d_ik / r_ik^3
+ *           + sum_{j != k} q_j H(d_kj) b_k - sum_{i != k} q_k H(d_ik) b_i,
+ * H(d) = -I / r^3 + 3 d d^T / r^5 (the Hessian of 1/|d|).  Pairs at distance
+ * 0 contribute nothing, as in the forward sum.  a or b may be NULL (zero).
+ * targets == NULL: all N outputs; otherwise the nt listed indices.
+ */
+void orc_direct_backward(int64_t N, const double *x, const double *q, const double *a,
+                         const double *b, int64_t nt, const int64_t *targets, double *dq,
+                         double *dx)
+{
+    int64_t nout = targets ? nt : N;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nout; ++t) {
+        int64_t k = targets ? targets[t] : t;
+        double g[3] = {0.0, 0.0, 0.0}, s_dq = 0.0, s_dx[3] = {0.0, 0.0, 0.0};
+        double bk[3] = {0.0, 0.0, 0.0};
+        if (b) for (int c = 0; c < 3; ++c) bk[c] = b[3 * k + c];
+        for (int64_t i = 0; i < N; ++i) {
+            double d[3];  /* d_ik = x_i - x_k */
+            for (int c = 0; c < 3; ++c) d[c] = x[3 * i + c] - x[3 * k + c];
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2;
+            double ai = a ? a[i] : 0.0;
+            double bi[3] = {0.0, 0.0, 0.0};
+            if (b) for (int c = 0; c < 3; ++c) bi[c] = b[3 * i + c];
+            /* potential and gradient at k (d_ki = -d_ik) */
+            for (int c = 0; c < 3; ++c) g[c] += q[i] * d[c] / r3;
+            /* dq_k */
+            s_dq += ai / r - (bi[0] * d[0] + bi[1] * d[1] + bi[2] * d[2]) / r3;
+            /* dx_k: a_i q_k d_ik / r^3 */
+            for (int c = 0; c < 3; ++c) s_dx[c] += ai * q[k] * d[c] / r3;
+            /* q_i H(d_ki) b_k - q_k H(d_ik) b_i; H is even in d */
+            double dbk = d[0] * bk[0] + d[1] * bk[1] + d[2] * bk[2];
+            double dbi = d[0] * bi[0] + d[1] * bi[1] + d[2] * bi[2];
+            for (int c = 0; c < 3; ++c) {
+                double Hbk = -bk[c] / r3 + 3.0 * d[c] * dbk / r5;
+                double Hbi = -bi[c] / r3 + 3.0 * d[c] * dbi / r5;
+                s_dx[c] += q[i] * Hbk - q[k] * Hbi;
+            }
+        }
+        double ak = a ? a[k] : 0.0;
+        dq[t] = s_dq;
+        for (int c = 0; c < 3; ++c) dx[3 * t + c] = ak * g[c] + s_dx[c];
     }
 }
 
@@ -917,6 +1048,192 @@ int orc_evaluate(orc_fmm *f, const double *q, int64_t nt, const int64_t *targets
 done:
     free(qs); free(M); free(L); free(ps); free(gs); free(want); free(need); free(inv);
     free(m2l); free(p2p); free(m2l_off); free(p2p_off);
+    return rc;
+}
+
+/*
+ * Far field of sources with charges cq and (optionally) dipoles cp (3 per
+ * source), sorted order: P2M (charge + dipole) on leaves, M2M bottom-up, M2L
+ * over the list (targets with need[c] only), L2L top-down.  L is returned
+ * zero except on needed cells.
+ */
+static int orc_far_field(const orc_fmm *f, const double *cq, const double *cp, const char *need,
+                         const orc_pair *m2l, const int64_t *m2l_off, double *M, double *L)
+{
+    const orc_mindex *mi = &f->mi;
+    int T = mi->nterms;
+    int64_t nc = f->ncells;
+    memset(M, 0, (size_t)nc * T * sizeof(double));
+    memset(L, 0, (size_t)nc * T * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (!orc_is_leaf(f, c)) continue;
+        double X[3];
+        orc_centre_d(f, c, X);
+        if (cp)
+            orc_p2m_dipole_mi(mi, (int)f->pcnt[c], f->u + 3 * f->pbeg[c], cq + f->pbeg[c],
+                              cp + 3 * f->pbeg[c], X, M + c * T);
+        else
+            orc_p2m_mi(mi, (int)f->pcnt[c], f->u + 3 * f->pbeg[c], cq + f->pbeg[c], X, M + c * T);
+    }
+    for (int64_t c = nc - 1; c >= 1; --c) {
+        double Xc[3], Xp[3];
+        int64_t p = f->parent[c];
+        orc_centre_d(f, c, Xc);
+        orc_centre_d(f, p, Xp);
+        orc_m2m_mi(mi, M + c * T, Xc, Xp, M + p * T);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (!need[c]) continue;
+        double Xt[3];
+        orc_centre_d(f, c, Xt);
+        for (int64_t e = m2l_off[c]; e < m2l_off[c + 1]; ++e) {
+            double Xs[3];
+            int64_t s = m2l[e].b;
+            orc_centre_d(f, s, Xs);
+            orc_m2l_mi(mi, M + s * T, Xs, Xt, L + c * T);
+        }
+    }
+    for (int64_t c = 1; c < nc; ++c) {
+        if (!need[c]) continue;
+        double Xc[3], Xp[3];
+        int64_t p = f->parent[c];
+        orc_centre_d(f, c, Xc);
+        orc_centre_d(f, p, Xp);
+        orc_l2l_mi(mi, L + p * T, Xp, Xc, L + c * T);
+    }
+    return 0;
+}
+
+/*
+ * FMM adjoint (see the header): for charges q and upstream gradients a = dL/dphi
+ * (N, may be NULL) and b = dL/dgrad (N x 3, may be NULL), caller order and
+ * physical units, returns dq = dL/dq and dx = dL/dx at all N particles
+ * (targets == NULL) or at the nt listed ones.  In normalised coordinates
+ * u = (x - c) / h the dipoles are b' = b / h, and then
+ *   dq = Psi_u / h,   dx = (a grad_u + H_u b' + q grad Psi_u) / h^2,
+ * where Psi_u is the field of charges a and dipoles b' and grad_u, H_u are the
+ * gradient and Hessian of the potential of the charges q.  Steps: the far
+ * field of q (P2M, M2M, M2L, L2L over the traversal's lists), the far field
+ * of (a, b'), then per wanted target L2P of both (gradient, Hessian-vector
+ * product, Psi and its gradient) and P2P over the P2P list:
+ *   Psi      += a_j / r + b'_j . d / r^3
+ *   grad Psi += -a_j d / r^3 + b'_j / r^3 - 3 (b'_j . d) d / r^5
+ *   grad     += -q_j d / r^3
+ *   H b'_i   += q_j (-b'_i / r^3 + 3 (d . b'_i) d / r^5),      d = u_i - u_j, r != 0.
+ */
+int orc_backward(orc_fmm *f, const double *q, const double *a, const double *b, int64_t nt,
+                 const int64_t *targets, double *dq, double *dx)
+{
+    if (!f->built) return -1;
+    const orc_mindex *mi = &f->mi;
+    int T = mi->nterms;
+    int64_t N = f->N, nc = f->ncells;
+    double ih = 1.0 / f->h, ih2 = ih * ih;
+    double *qs = (double *)malloc((size_t)N * sizeof(double));
+    double *as = (double *)calloc((size_t)N, sizeof(double));
+    double *bs = (double *)calloc((size_t)N * 3, sizeof(double));
+    double *Mq = (double *)malloc((size_t)nc * T * sizeof(double));
+    double *Lq = (double *)malloc((size_t)nc * T * sizeof(double));
+    double *Ma = (double *)malloc((size_t)nc * T * sizeof(double));
+    double *La = (double *)malloc((size_t)nc * T * sizeof(double));
+    double *out_q = (double *)calloc((size_t)N, sizeof(double));
+    double *out_x = (double *)calloc((size_t)N * 3, sizeof(double));
+    char *want = (char *)calloc((size_t)N, 1);
+    char *need = (char *)calloc((size_t)nc, 1);
+    int64_t *inv = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    orc_pair *m2l = NULL, *p2p = NULL;
+    int64_t *m2l_off = NULL, *p2p_off = NULL;
+    int rc = -1;
+    if (!qs || !as || !bs || !Mq || !Lq || !Ma || !La || !out_q || !out_x || !want || !need || !inv)
+        goto done;
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t i = f->perm[s];
+        qs[s] = q[i];
+        inv[i] = s;
+        if (a) as[s] = a[i];
+        if (b) for (int c = 0; c < 3; ++c) bs[3 * s + c] = b[3 * i + c] * ih;
+    }
+    if (targets) {
+        for (int64_t t = 0; t < nt; ++t) {
+            if (targets[t] < 0 || targets[t] >= N) goto done;
+            want[inv[targets[t]]] = 1;
+        }
+    } else {
+        memset(want, 1, (size_t)N);
+    }
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        if (orc_is_leaf(f, c)) {
+            for (int64_t j = f->pbeg[c]; j < f->pbeg[c] + f->pcnt[c]; ++j)
+                if (want[j]) { need[c] = 1; break; }
+        }
+        if (need[c] && f->parent[c] >= 0) need[f->parent[c]] = 1;
+    }
+    m2l = (orc_pair *)malloc((size_t)(f->m2l.n + 1) * sizeof(orc_pair));
+    m2l_off = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    p2p = (orc_pair *)malloc((size_t)(f->p2p.n + 1) * sizeof(orc_pair));
+    p2p_off = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    if (!m2l || !m2l_off || !p2p || !p2p_off) goto done;
+    memcpy(m2l, f->m2l.v, (size_t)f->m2l.n * sizeof(orc_pair));
+    qsort(m2l, (size_t)f->m2l.n, sizeof(orc_pair), orc_cmp_pair);
+    for (int64_t e = 0; e < f->m2l.n; ++e) m2l_off[m2l[e].a + 1]++;
+    for (int64_t c = 0; c < nc; ++c) m2l_off[c + 1] += m2l_off[c];
+    memcpy(p2p, f->p2p.v, (size_t)f->p2p.n * sizeof(orc_pair));
+    qsort(p2p, (size_t)f->p2p.n, sizeof(orc_pair), orc_cmp_pair);
+    for (int64_t e = 0; e < f->p2p.n; ++e) p2p_off[p2p[e].a + 1]++;
+    for (int64_t c = 0; c < nc; ++c) p2p_off[c + 1] += p2p_off[c];
+
+    orc_far_field(f, qs, NULL, need, m2l, m2l_off, Mq, Lq);
+    orc_far_field(f, as, bs, need, m2l, m2l_off, Ma, La);
+
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (!orc_is_leaf(f, c) || !need[c]) continue;
+        double Xt[3];
+        orc_centre_d(f, c, Xt);
+        for (int64_t i = f->pbeg[c]; i < f->pbeg[c] + f->pcnt[c]; ++i) {
+            if (!want[i]) continue;
+            const double *ui = f->u + 3 * i, *bi = bs + 3 * i;
+            double phi_q = 0.0, g[3] = {0.0, 0.0, 0.0}, hb[3] = {0.0, 0.0, 0.0};
+            double psi = 0.0, gpsi[3] = {0.0, 0.0, 0.0};
+            orc_l2p_mi(mi, Lq + c * T, Xt, 1, ui, &phi_q, g);
+            orc_l2p_hess_mi(mi, Lq + c * T, Xt, ui, bi, hb);
+            orc_l2p_mi(mi, La + c * T, Xt, 1, ui, &psi, gpsi);
+            for (int64_t e = p2p_off[c]; e < p2p_off[c + 1]; ++e) {
+                int64_t s = p2p[e].b;
+                for (int64_t j = f->pbeg[s]; j < f->pbeg[s] + f->pcnt[s]; ++j) {
+                    const double *uj = f->u + 3 * j, *bj = bs + 3 * j;
+                    double d[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 == 0.0) continue;
+                    double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2;
+                    double bjd = bj[0] * d[0] + bj[1] * d[1] + bj[2] * d[2];
+                    double bid = bi[0] * d[0] + bi[1] * d[1] + bi[2] * d[2];
+                    psi += as[j] / r + bjd / r3;
+                    for (int k = 0; k < 3; ++k) {
+                        gpsi[k] += -as[j] * d[k] / r3 + bj[k] / r3 - 3.0 * bjd * d[k] / r5;
+                        g[k] += -qs[j] * d[k] / r3;
+                        hb[k] += qs[j] * (-bi[k] / r3 + 3.0 * bid * d[k] / r5);
+                    }
+                }
+            }
+            out_q[i] = psi * ih;
+            for (int k = 0; k < 3; ++k) out_x[3 * i + k] = (as[i] * g[k] + hb[k] + qs[i] * gpsi[k]) * ih2;
+        }
+    }
+    {
+        int64_t nout = targets ? nt : N;
+        for (int64_t t = 0; t < nout; ++t) {
+            int64_t s = targets ? inv[targets[t]] : inv[t];
+            dq[t] = out_q[s];
+            for (int k = 0; k < 3; ++k) dx[3 * t + k] = out_x[3 * s + k];
+        }
+    }
+    rc = 0;
+done:
+    free(qs); free(as); free(bs); free(Mq); free(Lq); free(Ma); free(La); free(out_q); free(out_x);
+    free(want); free(need); free(inv); free(m2l); free(p2p); free(m2l_off); free(p2p_off);
     return rc;
 }
 

@@ -44,6 +44,15 @@ MUTANTS = [
     ("normalisation_no_margin", "h = h * (1.0 + 0x1p-20);", "h = h * 1.0;", "test_oracle_tree.py"),
     ("m2l_list_dropped_term", "L[tm->t] += tm->coef * M[tm->u] * b[tm->j];",
      "if (tm->u != 1) L[tm->t] += tm->coef * M[tm->u] * b[tm->j];", "test_oracle_expansions.py"),
+    ("dipole_p2m_sign", "M[t] += p[3 * j + c] * orc_mpow(d, km) / orc_mfact(km);",
+     "M[t] -= p[3 * j + c] * orc_mpow(d, km) / orc_mfact(km);", "test_oracle_adjoint.py"),
+    ("hessian_l2p_diagonal_factor", "f *= km[b];", "f *= k[b];", "test_oracle_adjoint.py"),
+    ("backward_p2p_hessian_sign", "hb[k] += qs[j] * (-bi[k] / r3 + 3.0 * bid * d[k] / r5);",
+     "hb[k] += qs[j] * (bi[k] / r3 + 3.0 * bid * d[k] / r5);", "test_oracle_adjoint.py"),
+    ("backward_dipole_field_dropped", "psi += as[j] / r + bjd / r3;", "psi += as[j] / r;",
+     "test_oracle_adjoint.py"),
+    ("direct_backward_dq_sign", "s_dq += ai / r - (bi[0] * d[0]", "s_dq += ai / r + (bi[0] * d[0]",
+     "test_oracle_adjoint.py"),
 ]
 
 
