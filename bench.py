@@ -11,6 +11,10 @@ P2P + L2P + scatter) with inputs resident in HBM; L2 is flushed (256 MiB
 write) before every timed step, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--dist uniform|plummer] [--kahan] [--N ..] [--P ..] [--theta ..] [--ncrit ..]
+
+--dist plummer --kahan --N 4194304 --P 4 --theta 0.4 times the adaptive workload
+(Plummer sphere, charges 1/N, compensated P2P accumulation) the same way.
 
 Multi-GPU: the path does not shard (one FMM per GPU), so N GPUs run N
 independent replicas; value = all evaluations / max-over-ranks time.
@@ -45,20 +49,26 @@ def parse():
     ap.add_argument("--P", type=int, default=8)
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--ncrit", type=int, default=64)
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "plummer"])
+    ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def workload(N):
+def workload(a):
     from paper_1209_3516_gb300 import inputs
-    return inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    if a.dist == "plummer":
+        return inputs.plummer(a.N, inputs.SEED_BASE + 2)
+    return inputs.uniform_cube(a.N, inputs.SEED_BASE + 1)
 
 
 def config(a):
-    return {"workload": "uniform cube N=%d, P=%d, theta=%.2f, ncrit=%d, potential+gradient, one charge vector"
-                        % (a.N, a.P, a.theta, a.ncrit),
-            "N": a.N, "P": a.P, "theta": a.theta, "ncrit": a.ncrit,
+    what = ("uniform cube" if a.dist == "uniform" else
+            "Plummer sphere (a=1, r<=100, charges 1/N)")
+    return {"workload": "%s N=%d, P=%d, theta=%.2f, ncrit=%d, potential+gradient, one charge vector%s"
+                        % (what, a.N, a.P, a.theta, a.ncrit, ", compensated P2P" if a.kahan else ""),
+            "N": a.N, "P": a.P, "theta": a.theta, "ncrit": a.ncrit, "dist": a.dist, "kahan": a.kahan,
             "step": "fmm_build + fmm_evaluate",
             "l2": "flushed before every timed step (256 MiB write)"}
 
@@ -67,9 +77,19 @@ def config(a):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample(a, x, q):
-    """Particles of the workload in the octant [0, 1/2)^3: same density, same leaves."""
+    """Uniform cube: the particles in the octant [0, 1/2)^3 (same density, same
+    leaves).  Plummer: the first N/16 particles (a Plummer sphere of N/16)."""
+    if a.dist == "plummer":
+        n = max(1, a.N // 16)
+        return x[:n], q[:n]
     m = np.all(x < 0.5, axis=1)
     return x[m], q[m]
+
+
+def sample_words(a, n):
+    if a.dist == "plummer":
+        return "the first %d particles of the workload (a Plummer sphere of that size)" % n
+    return "the %d particles of the workload in the octant [0,1/2)^3 (same density and leaves)" % n
 
 
 def time_oracle(a, xs, qs, reps=1):
@@ -89,9 +109,8 @@ def cpu_baseline(a, x, q, reps=1):
     ts = time_oracle(a, xs, qs, reps)
     t_full = statistics.median(ts) * a.N / xs.shape[0]
     return {"value": 1.0 / t_full, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "FP64 oracle FMM (build + evaluate, same P/theta/ncrit) on the %d particles of the "
-                      "workload in the octant [0,1/2)^3 (same density and leaves), time scaled by N/%d"
-                      % (xs.shape[0], xs.shape[0]),
+            "sample": "FP64 oracle FMM (build + evaluate, same P/theta/ncrit) on %s, time scaled by N/%d"
+                      % (sample_words(a, xs.shape[0]), xs.shape[0]),
             "seconds_per_sample": statistics.median(ts)}
 
 
@@ -103,6 +122,8 @@ def p2p_traffic(a):
     try:
         pj = json.load(open(prof))
         if (pj.get("N"), pj.get("P"), pj.get("theta"), pj.get("ncrit")) != (a.N, a.P, a.theta, a.ncrit):
+            return None
+        if (pj.get("dist", "uniform"), pj.get("kahan", False)) != (a.dist, a.kahan):
             return None
         h = hashlib.sha256()
         for f in pj["sources"]:
@@ -221,7 +242,7 @@ def run_reference(a):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     import oracle
-    x, q = workload(a.N)
+    x, q = workload(a)
     xs, qs = oracle_sample(a, x, q)
     time_oracle(a, xs, qs, reps=max(0, a.warmup))
     t0 = time.perf_counter()
@@ -234,8 +255,8 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "each step: FP64 oracle FMM (build + evaluate) on the %d particles of the "
-                                       "workload in [0,1/2)^3, time scaled by N/%d" % (xs.shape[0], xs.shape[0])},
+                             "sample": "each step: FP64 oracle FMM (build + evaluate) on %s, time scaled by N/%d"
+                                       % (sample_words(a, xs.shape[0]), xs.shape[0])},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line))
@@ -250,14 +271,14 @@ def run_ours(a):
     dev = local if torch.cuda.device_count() > local else 0
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    x, q = workload(a.N)
+    x, q = workload(a)
     q32 = q.astype(np.float32)
     xd = torch.from_numpy(x).cuda()
     qd = torch.from_numpy(q32).cuda()
     phi = torch.empty(a.N, dtype=torch.float32, device="cuda")
     grad = torch.empty(a.N, 3, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, timing=True)
+    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, kahan=a.kahan, timing=True)
 
     def step():
         h.build(xd)

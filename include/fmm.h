@@ -83,6 +83,7 @@ struct fmm_stats {
     double ms_build, ms_evaluate;          /* device time of the last build / evaluate */
     double ms_phase[FMM_NPHASES];          /* per phase, when FMM_FLAG_TIMING is set */
     int64_t kernel_launches;               /* CUDA kernels launched by this handle since creation */
+    double ms_backward;                    /* device time of the last fmm_backward */
 };
 
 /*
@@ -144,14 +145,25 @@ int fmm_evaluate_host(fmm_handle *h, const double *x_host, const float *q_host, 
 int fmm_energy(fmm_handle *h, double *E);
 
 /*
- * fmm_backward -- adjoint of the last evaluate for upstream gradients dphi
- * (N FP32, may be NULL) and dgrad (N x 3 FP32, may be NULL) of a loss L(phi, grad).
- *   dq  out (device, N FP32, may be NULL): dL/dq_j = sum_i dphi_i / r_ij
- *       - sum_i dgrad_i . (x_i - x_j) / r_ij^3, i.e. the potential at x_j of the
- *       charges dphi plus that of dipoles dgrad (the kernel is symmetric).
- *   dx  out (device, N x 3 FP32, may be NULL): dL/dx_i.
- * Returns FMM_ERR_UNSUPPORTED for the parts this build does not provide
- * (see fmm_last_error_string).
+ * fmm_backward -- adjoint of the last fmm_evaluate on this handle (same x and q),
+ * for the upstream gradients of a scalar loss L(phi, grad):
+ *   dphi  device, N FP32, dL/dphi (caller order); NULL = zero.
+ *   dgrad device, N x 3 FP32, dL/dgrad; NULL = zero.
+ *   dq    out, device, N FP32, or NULL:  dL/dq_k = Psi(x_k), the potential at x_k of
+ *         charges dphi_i and dipoles dgrad_i at the x_i:
+ *         Psi(x) = sum_i dphi_i / |x - x_i| + sum_i dgrad_i . (x - x_i) / |x - x_i|^3.
+ *   dx    out, device, N x 3 FP32, or NULL:
+ *         dL/dx_k = dphi_k grad_k + H_k dgrad_k + q_k grad Psi(x_k),
+ *         H_k the Hessian of the potential at x_k (pairs at distance 0 excluded).
+ * dq and dx must not both be NULL.  The paper has no adjoint: these are the
+ * derivatives of the sums of Sec. 3.2, evaluated with the same method: the
+ * adjoint sources get a dipole P2M and the same M2M, M2L (same lists) and L2L;
+ * one kernel then does the adjoint P2P over the P2P list, the L2P terms of both
+ * local expansions (value, gradient and Hessian-vector product) and the
+ * scatter.  The handle's forward local expansions and sorted charges are used,
+ * so no evaluate may come between the fmm_evaluate being differentiated and
+ * this call.  Asynchronous on the handle's stream (the first call after a build
+ * synchronises once to size its work items).  FMM_ERR_STATE before an evaluate.
  */
 int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq, float *dx);
 

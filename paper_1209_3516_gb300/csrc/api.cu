@@ -96,6 +96,7 @@ static int do_build(Handle &h, const double *x)
 {
     h.built = false;
     h.evaluated = false;
+    h.backward_done = false;
     const int ev0 = 2 * kPhases, ev1 = 2 * kPhases + 1;
     if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
     FMM_TRY(build_keys(h, x));
@@ -118,10 +119,11 @@ static int do_evaluate(Handle &h, const float *q, float *phi, float *grad)
     FMM_TRY(evaluate_upward(h, q));
     phase_end(h, FMM_PHASE_UPWARD);
     phase_begin(h, FMM_PHASE_M2L);
-    FMM_TRY(evaluate_m2l(h));
+    FMM_TRY(h.L.reserve((size_t)h.ncells * h.TP * sizeof(float)));
+    FMM_TRY(evaluate_m2l(h, h.M.as<float>(), h.L.as<float>()));
     phase_end(h, FMM_PHASE_M2L);
     phase_begin(h, FMM_PHASE_DOWNWARD);
-    FMM_TRY(evaluate_downward(h));
+    FMM_TRY(evaluate_downward(h, h.L.as<float>()));
     phase_end(h, FMM_PHASE_DOWNWARD);
     phase_begin(h, FMM_PHASE_P2P);
     FMM_TRY(evaluate_p2p(h, phi, grad));
@@ -286,16 +288,32 @@ int fmm_energy(fmm_handle *w, double *E)
 
 int fmm_backward(fmm_handle *w, const float *dphi, const float *dgrad, float *dq, float *dx)
 {
-    (void)dphi;
-    (void)dgrad;
-    (void)dq;
-    (void)dx;
     if (!w) {
         set_error("fmm_backward: null handle");
         return FMM_ERR_ARG;
     }
-    set_error("fmm_backward: not available in this build");
-    return FMM_ERR_UNSUPPORTED;
+    if (!dq && !dx) {
+        set_error("fmm_backward: dq and dx are both NULL");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    if (!h.evaluated) {
+        set_error("fmm_backward: no evaluation to differentiate");
+        return FMM_ERR_STATE;
+    }
+    DeviceGuard guard(h.device);
+    const int ev0 = 2 * kPhases + 4, ev1 = 2 * kPhases + 5;
+    if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
+    // far field of the adjoint sources: dipole P2M, M2M, M2L, L2L (same lists)
+    FMM_TRY(adjoint_upward(h, dphi, dgrad));
+    FMM_TRY(h.La.reserve((size_t)h.ncells * h.TP * sizeof(float)));
+    FMM_TRY(evaluate_m2l(h, h.Ma.as<float>(), h.La.as<float>()));
+    FMM_TRY(evaluate_downward(h, h.La.as<float>()));
+    // near field, far-field terms at the targets and the scatter
+    FMM_TRY(adjoint_p2p(h, dq, dx));
+    if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
+    h.backward_done = true;
+    return FMM_OK;
 }
 
 int fmm_stats(fmm_handle *w, struct fmm_stats *s)
@@ -322,6 +340,8 @@ int fmm_stats(fmm_handle *w, struct fmm_stats *s)
         float ms = 0.f;
         if (h.evaluated && cudaEventElapsedTime(&ms, h.ev[2 * kPhases + 2], h.ev[2 * kPhases + 3]) == cudaSuccess)
             s->ms_evaluate = ms;
+        if (h.backward_done && cudaEventElapsedTime(&ms, h.ev[2 * kPhases + 4], h.ev[2 * kPhases + 5]) == cudaSuccess)
+            s->ms_backward = ms;
         if (h.flags & FMM_FLAG_TIMING)
             for (int p = 0; p < kPhases; ++p) {
                 ms = 0.f;

@@ -77,10 +77,13 @@ template <int T, int TP> __device__ __forceinline__ void warp_store_vec(const fl
 
 // ---------------------------------------------------------------------------
 // P2M: Mb_k(C) = sum_j q_j w_k((X_C - u_j) / s_C)
+// With kDipole (adjoint sources, adj[j] = (a_j, p_j)): charges a_j and dipoles
+// p_j, whose multipole is p . grad_u of a unit charge's:
+//   Mb_k(C) += a_j w_k(v_j) - (1/s_C) sum_c p_{j,c} w_{k - e_c}(v_j),  v_j = (X_C - u_j) / s_C.
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, bool kDipole>
 __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const int *pcnt, const int *level,
-                      const int *parent, const float4 *geom, const float4 *pos, float *M)
+                      const int *parent, const float4 *geom, const float4 *pos, const float4 *adj, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -100,8 +103,27 @@ __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const 
         const float4 p = pos[j];
         float w[T];
         taylor_monomials<P>(fmaf(-p.x, inv_s, ox), fmaf(-p.y, inv_s, oy), fmaf(-p.z, inv_s, oz), w);
+        if constexpr (kDipole) {
+            const float4 ab = adj[j];
+            const float px = -ab.y * inv_s, py = -ab.z * inv_s, pz = -ab.w * inv_s;
 #pragma unroll
-        for (int i = 0; i < T; ++i) acc[i] = fmaf(p.w, w[i], acc[i]);
+            for (int n = 0; n < P; ++n)
+#pragma unroll
+                for (int ka = n; ka >= 0; --ka)
+#pragma unroll
+                    for (int kb = n - ka; kb >= 0; --kb) {
+                        const int kc = n - ka - kb;
+                        const int i = MI<P>::idx(ka, kb, kc);
+                        float v = ab.x * w[i];
+                        if (ka > 0) v = fmaf(px, w[MI<P>::idx(ka - 1, kb, kc)], v);
+                        if (kb > 0) v = fmaf(py, w[MI<P>::idx(ka, kb - 1, kc)], v);
+                        if (kc > 0) v = fmaf(pz, w[MI<P>::idx(ka, kb, kc - 1)], v);
+                        acc[i] += v;
+                    }
+        } else {
+#pragma unroll
+            for (int i = 0; i < T; ++i) acc[i] = fmaf(p.w, w[i], acc[i]);
+        }
     }
     if constexpr (T <= 64) {
         constexpr int K = Pad32Pow2<T>::value / 32;
@@ -397,62 +419,85 @@ __global__ void k_gather_q(int64_t n, const int *perm, const float *q, float4 *p
     if (s < n) pos[s].w = q[perm[s]];
 }
 
+template <int P> static int m2m_levels(Handle &h, float *M)
+{
+    for (int l = h.nlevels - 2; l >= 0; --l) {
+        const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
+        ++h.launches;
+        if (P >= 8)
+            k_m2m_sep<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
+                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), M);
+        else
+            k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
+                                                           h.c_geom.as<float4>(), M);
+    }
+    FMM_CHECK_LAUNCH("upward pass");
+    return FMM_OK;
+}
+
 template <int P> static int upward_impl(Handle &h, const float *q)
 {
     const int nl = (int)h.nleaves;
     ++h.launches;
     k_gather_q<<<ceil_div(h.N, 256), 256, 0, h.stream>>>(h.N, h.perm.as<int>(), q, h.pos.as<float4>());
     ++h.launches;
-    k_p2m<P><<<ceil_div((int64_t)nl * 32, 128), 128, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
-                                                                    h.c_pcnt.as<int>(), h.c_level.as<int>(),
-                                                                    h.c_parent.as<int>(), h.c_geom.as<float4>(),
-                                                                    h.pos.as<float4>(), h.M.as<float>());
-    for (int l = h.nlevels - 2; l >= 0; --l) {
-        const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
-        ++h.launches;
-        if (P >= 8)
-            k_m2m_sep<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
-                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), h.M.as<float>());
-        else
-            k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
-                                                           h.c_geom.as<float4>(), h.M.as<float>());
-    }
-    FMM_CHECK_LAUNCH("upward pass");
-    return FMM_OK;
+    k_p2m<P, false><<<ceil_div((int64_t)nl * 32, 128), 128, 0, h.stream>>>(
+        nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(), h.c_parent.as<int>(),
+        h.c_geom.as<float4>(), h.pos.as<float4>(), nullptr, h.M.as<float>());
+    return m2m_levels<P>(h, h.M.as<float>());
 }
 
-template <int P> static int m2l_impl(Handle &h)
+// adj[s] = (dphi[perm[s]], dgrad[perm[s]] / h): charges and dipoles of the adjoint
+// field in normalised coordinates (either input may be absent: zero)
+__global__ void k_gather_adj(int64_t n, const int *perm, const float *dphi, const float *dgrad, float inv_h,
+                             float4 *adj)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (dphi) v.x = dphi[i];
+    if (dgrad) {
+        v.y = dgrad[3 * i] * inv_h;
+        v.z = dgrad[3 * i + 1] * inv_h;
+        v.w = dgrad[3 * i + 2] * inv_h;
+    }
+    adj[s] = v;
+}
+
+template <int P> static int adjoint_upward_impl(Handle &h, const float *dphi, const float *dgrad)
+{
+    const int nl = (int)h.nleaves;
+    ++h.launches;
+    k_gather_adj<<<ceil_div(h.N, 256), 256, 0, h.stream>>>(h.N, h.perm.as<int>(), dphi, dgrad,
+                                                          (float)(1.0 / h.norm_host[3]), h.adj.as<float4>());
+    ++h.launches;
+    k_p2m<P, true><<<ceil_div((int64_t)nl * 32, 128), 128, 0, h.stream>>>(
+        nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(), h.c_parent.as<int>(),
+        h.c_geom.as<float4>(), h.pos.as<float4>(), h.adj.as<float4>(), h.Ma.as<float>());
+    return m2m_levels<P>(h, h.Ma.as<float>());
+}
+
+template <int P> static int m2l_impl(Handle &h, const float *M, float *L)
 {
     const int nc = (int)h.ncells;
     ++h.launches;
     k_m2l<P><<<ceil_div((int64_t)nc * 32, 128), 128, 0, h.stream>>>(nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(),
-                                                                    h.c_level.as<int>(), h.c_geom.as<float4>(),
-                                                                    h.M.as<float>(), h.L.as<float>());
+                                                                    h.c_level.as<int>(), h.c_geom.as<float4>(), M, L);
     FMM_CHECK_LAUNCH("m2l");
     return FMM_OK;
 }
 
-template <int P> static int downward_impl(Handle &h)
+template <int P> static int downward_impl(Handle &h, float *L)
 {
     for (int l = 1; l < h.nlevels; ++l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
         ++h.launches;
-        k_l2l<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_parent.as<int>(), h.c_geom.as<float4>(),
-                                                       h.L.as<float>());
+        k_l2l<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_parent.as<int>(), h.c_geom.as<float4>(), L);
     }
     FMM_CHECK_LAUNCH("downward pass");
     return FMM_OK;
 }
-
-#define FMM_DISPATCH_P(P, CALL)                                               \
-    switch (P) {                                                              \
-    case 3: return CALL<3>;                                                   \
-    case 4: return CALL<4>;                                                   \
-    case 5: return CALL<5>;                                                   \
-    case 6: return CALL<6>;                                                   \
-    case 8: return CALL<8>;                                                   \
-    default: set_error("expansion order not compiled"); return FMM_ERR_UNSUPPORTED; \
-    }
 
 int evaluate_upward(Handle &h, const float *q)
 {
@@ -467,27 +512,40 @@ int evaluate_upward(Handle &h, const float *q)
     }
 }
 
-int evaluate_m2l(Handle &h)
+int evaluate_m2l(Handle &h, const float *M, float *L)
 {
-    FMM_TRY(h.L.reserve((size_t)h.ncells * h.TP * sizeof(float)));
     switch (h.P) {
-    case 3: return m2l_impl<3>(h);
-    case 4: return m2l_impl<4>(h);
-    case 5: return m2l_impl<5>(h);
-    case 6: return m2l_impl<6>(h);
-    case 8: return m2l_impl<8>(h);
+    case 3: return m2l_impl<3>(h, M, L);
+    case 4: return m2l_impl<4>(h, M, L);
+    case 5: return m2l_impl<5>(h, M, L);
+    case 6: return m2l_impl<6>(h, M, L);
+    case 8: return m2l_impl<8>(h, M, L);
     default: set_error("expansion order not compiled"); return FMM_ERR_UNSUPPORTED;
     }
 }
 
-int evaluate_downward(Handle &h)
+int evaluate_downward(Handle &h, float *L)
 {
     switch (h.P) {
-    case 3: return downward_impl<3>(h);
-    case 4: return downward_impl<4>(h);
-    case 5: return downward_impl<5>(h);
-    case 6: return downward_impl<6>(h);
-    case 8: return downward_impl<8>(h);
+    case 3: return downward_impl<3>(h, L);
+    case 4: return downward_impl<4>(h, L);
+    case 5: return downward_impl<5>(h, L);
+    case 6: return downward_impl<6>(h, L);
+    case 8: return downward_impl<8>(h, L);
+    default: set_error("expansion order not compiled"); return FMM_ERR_UNSUPPORTED;
+    }
+}
+
+int adjoint_upward(Handle &h, const float *dphi, const float *dgrad)
+{
+    FMM_TRY(h.adj.reserve((size_t)h.N * sizeof(float4)));
+    FMM_TRY(h.Ma.reserve((size_t)h.ncells * h.TP * sizeof(float)));
+    switch (h.P) {
+    case 3: return adjoint_upward_impl<3>(h, dphi, dgrad);
+    case 4: return adjoint_upward_impl<4>(h, dphi, dgrad);
+    case 5: return adjoint_upward_impl<5>(h, dphi, dgrad);
+    case 6: return adjoint_upward_impl<6>(h, dphi, dgrad);
+    case 8: return adjoint_upward_impl<8>(h, dphi, dgrad);
     default: set_error("expansion order not compiled"); return FMM_ERR_UNSUPPORTED;
     }
 }

@@ -146,6 +146,14 @@ struct Handle {
     // expansions and outputs
     DevBuf M, L;          // float[ncells * TP]
 
+    // adjoint (fmm_backward): sorted upstream gradients, expansions of the
+    // adjoint sources, work items of <= 8 targets
+    DevBuf adj;           // float4[N] (dL/dphi, h^-1 dL/dgrad) in sorted order
+    DevBuf Ma, La;        // float[ncells * TP]
+    DevBuf adj_items;     // int4 work items
+    int64_t n_adj_items = 0;
+    bool adj_items_ready = false;
+
     DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
     DevBuf energy_part;   // double partials
 
@@ -156,10 +164,11 @@ struct Handle {
     int64_t launches = 0;
 
     // timing
-    cudaEvent_t ev[2 * kPhases + 4] = {};
+    cudaEvent_t ev[2 * kPhases + 6] = {};   // phases, build, evaluate, backward
     bool events_ready = false;
     float ms_phase[kPhases] = {};
     float ms_build = 0.f, ms_eval = 0.f;
+    bool backward_done = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -176,10 +185,13 @@ int build_keys(Handle &h, const double *x);       // bbox, normalise, Morton, so
 int build_tree(Handle &h, const double *x);       // cells, geometry, leaf-local positions
 int build_lists(Handle &h);                       // DTT + grouping
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
+int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items);   // items of <= g targets
 
 int evaluate_upward(Handle &h, const float *q);   // gather q, P2M, M2M
-int evaluate_m2l(Handle &h);
-int evaluate_downward(Handle &h);                 // L2L
+int evaluate_m2l(Handle &h, const float *M, float *L);
+int evaluate_downward(Handle &h, float *L);       // L2L
+int adjoint_upward(Handle &h, const float *dphi, const float *dgrad);   // gather (a, b / h), P2M, M2M into Ma
+int adjoint_p2p(Handle &h, float *dq, float *dx); // adjoint P2P + L2P terms + scatter
 int evaluate_p2p(Handle &h, float *phi, float *grad);   // P2P + L2P + scatter
 int energy_reduce(Handle &h, double *E);
 

@@ -23,7 +23,9 @@
 //     expansion is added, units restored (phi / h, grad / h^2) and the result
 //     written at the caller's index.
 // With FMM_FLAG_KAHAN each lane keeps its per-target sums as (sum, compensation)
-// pairs updated once per 8 sources (plain FP32 inside the block of 8).
+// pairs, updated once per staged chunk (plain FP32 over the lane's 8 sources of
+// the chunk, then one compensated add); work items then hold at most 8 targets
+// so that the three accumulator sets stay in registers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +33,7 @@
 #include "device_util.cuh"
 #include "fmm_internal.cuh"
 #include "mi.cuh"
+#include "p2p_common.cuh"
 
 namespace fmm {
 
@@ -38,6 +41,7 @@ namespace fmm {
 #define FMM_P2P_G 16
 #endif
 constexpr int kP2PG = FMM_P2P_G;   // targets per work item (multiple of 4, at most 16)
+constexpr int kP2PGKahan = 8;      // targets per work item with compensated accumulation
 constexpr int kP2PThreads = 128;
 
 #ifndef FMM_P2P_SLOTS
@@ -53,26 +57,25 @@ constexpr int kSlots = FMM_P2P_SLOTS;   // staged source particles per buffer
 constexpr int kP2PUnroll = FMM_P2P_UNROLL;   // staged sources per lane per loop iteration
 constexpr int kP2PSmem = (kP2PThreads / 32) * 4 * kSlots * (int)sizeof(float4);   // 2 buffers x (particles + shifts)
 
-__device__ __forceinline__ int frame_of(const int *parent, int c) { return parent[c] >= 0 ? parent[c] : c; }
 
 // Work items: one per slice of <= 16 targets of a leaf, slices balanced in size;
 // item = (leaf cell, first target, target count, index of the leaf in the leaf list).
-__global__ void k_p2p_item_count(int nleaves, const int *leaf_list, const int *pcnt, unsigned *cnt)
+__global__ void k_p2p_item_count(int nleaves, const int *leaf_list, const int *pcnt, int g, unsigned *cnt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nleaves) return;
     const int nt = pcnt[leaf_list[i]];
-    cnt[i] = (unsigned)((nt + kP2PG - 1) / kP2PG);
+    cnt[i] = (unsigned)((nt + g - 1) / g);
 }
 
-__global__ void k_p2p_item_write(int nleaves, const int *leaf_list, const int *pbeg, const int *pcnt,
+__global__ void k_p2p_item_write(int nleaves, const int *leaf_list, const int *pbeg, const int *pcnt, int g,
                                  const unsigned *off, int4 *items)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nleaves) return;
     const int c = leaf_list[i];
     const int nt = pcnt[c], b = pbeg[c];
-    const int ns = (nt + kP2PG - 1) / kP2PG;
+    const int ns = (nt + g - 1) / g;
     for (int k = 0; k < ns; ++k) {
         const int t0 = (int)((int64_t)nt * k / ns), t1 = (int)((int64_t)nt * (k + 1) / ns);
         items[off[i] + k] = make_int4(c, b + t0, t1 - t0, i);
@@ -193,59 +196,6 @@ __device__ __forceinline__ void p2p_tile(const float4 &s, const float2 *ntx, con
     }
 }
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Warp-uniform cursor over an item's source runs, filling staging buffers.
-struct RunCursor {
-    int e, e1, o, pb, cnt;
-    float shx, shy, shz;
-    __device__ __forceinline__ void load(const float4 *run, const int *run_end)
-    {
-        if (e < e1) {
-            const float4 r = run[e];
-            shx = r.x;
-            shy = r.y;
-            shz = r.z;
-            pb = __float_as_int(r.w);
-            cnt = run_end[e] - pb;
-        }
-    }
-    // Copy up to kSlots particles into part (cp.async) with their frame shift in
-    // shift; *self is set when the copied particles overlap [tb0, tb1).
-    __device__ __forceinline__ int stage(const float4 *run, const int *run_end, const float4 *pos, float4 *part,
-                                         float4 *shift, int tb0, int tb1, bool *self)
-    {
-        const int lane = (int)lane_id();
-        int slots = 0;
-        bool sf = false;
-        while (slots < kSlots && e < e1) {
-            const int m = min(cnt - o, kSlots - slots);
-            const int begin = pb + o;
-            sf |= begin < tb1 && begin + m > tb0;
-            const float4 sh = make_float4(shx, shy, shz, 0.0f);
-            for (int i = lane; i < m; i += 32) {
-                cp_async16(part + slots + i, pos + begin + i);
-                shift[slots + i] = sh;
-            }
-            slots += m;
-            o += m;
-            if (o == cnt) {
-                ++e;
-                o = 0;
-                load(run, run_end);
-            }
-        }
-        *self = sf;
-        return slots;
-    }
-};
-
 // The source stream of one work item: double-buffered staging (the next chunk is
 // copied while the current one is used) and NT targets per staged source.
 // With kKahan the per-chunk partial sums (blk) are added to v with Kahan
@@ -257,13 +207,14 @@ __device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, co
 {
     const int lane = (int)lane_id();
     bool self_cur = false, self_next = false;
-    int n_cur = cur.stage(run, run_end, pos, buf, buf + kSlots, lb0, lb1, &self_cur);
+    int n_cur = cur.stage<kSlots, false>(run, run_end, pos, nullptr, buf, nullptr, buf + kSlots, lb0, lb1, &self_cur);
     cp_async_commit();
     for (int c = 0; n_cur > 0; ++c) {
         float4 *cur_part = buf + (c & 1) * (2 * kSlots);
         float4 *cur_shift = cur_part + kSlots;
         float4 *nx = buf + ((c + 1) & 1) * (2 * kSlots);
-        const int n_next = cur.stage(run, run_end, pos, nx, nx + kSlots, lb0, lb1, &self_next);
+        const int n_next =
+            cur.stage<kSlots, false>(run, run_end, pos, nullptr, nx, nullptr, nx + kSlots, lb0, lb1, &self_next);
         cp_async_commit();
         cp_async_wait_1();
         __syncwarp();
@@ -298,7 +249,7 @@ __device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, co
     }
 }
 
-template <int P, bool kKahan>
+template <int P, bool kKahan, int G>
 __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nitems, const int4 *items, const unsigned *roff,
                                                      const float4 *run, const int *run_end, const float4 *pos,
                                                      const int *pbeg, const int *pcnt, const int *level,
@@ -306,7 +257,7 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
                                                      const int *perm, float phi_scale, float grad_scale, float *phi,
                                                      float *grad, float *phi_sorted)
 {
-    constexpr int G = kP2PG;
+    static_assert(G % 4 == 0 && G <= 16, "targets per item");
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
     extern __shared__ float4 p2p_smem[];
     const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -340,19 +291,21 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     }
 
     RunCursor cur;
-    cur.e = (int)roff[it.w];
-    cur.e1 = (int)roff[it.w + 1];
-    cur.o = 0;
-    cur.pb = 0;
-    cur.cnt = 0;
-    cur.shx = cur.shy = cur.shz = 0.f;
-    cur.load(run, run_end);
+    cur.init(roff, it.w, run, run_end);
     // the item computes ceil(tc / 4) * 4 targets (extra ones repeat the last target)
-    switch ((tc + 3) >> 2) {
-    case 1: p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
-    case 2: p2p_stream<8, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
-    case 3: p2p_stream<(G >= 12 ? 12 : 8), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
-    default: p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk); break;
+    const int nt4 = (tc + 3) >> 2;
+    if (nt4 == 1) {
+        p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (G > 8 && nt4 == 2) {
+        p2p_stream<8, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (G > 12 && nt4 == 3) {
+        p2p_stream<(G > 12 ? 12 : G), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else {
+        p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    }
+    if (kKahan) {   // fold the outstanding compensation into the sums
+#pragma unroll
+        for (int i = 0; i < 2 * G; ++i) a[i] = make_float2(a[i].x - comp[i].x, a[i].y - comp[i].y);
     }
     // v[4 g + k]: component k of target g (zero-padded to 16 targets)
     float v[64];
@@ -417,11 +370,31 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     }
 }
 
+// Work items of at most g targets over the leaf list (g = targets per warp item).
+int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items)
+{
+    const int nl = (int)h.nleaves;
+    FMM_TRY(h.c_tmp.reserve((size_t)(2 * nl + 1) * sizeof(unsigned)));
+    unsigned *cnt = h.c_tmp.as<unsigned>(), *off = cnt + nl, *tot = off + nl;
+    ++h.launches;
+    k_p2p_item_count<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pcnt.as<int>(), g, cnt);
+    FMM_TRY(scan_exclusive_u32(h, cnt, off, nl, tot));
+    FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    n_items = h.pinned->level_total;
+    FMM_TRY(items.reserve(std::max<int64_t>(n_items, 1) * sizeof(int4)));
+    ++h.launches;
+    k_p2p_item_write<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
+                                                              h.c_pcnt.as<int>(), g, off, items.as<int4>());
+    FMM_CHECK_LAUNCH("p2p items");
+    return FMM_OK;
+}
+
 int build_p2p_items(Handle &h)
 {
     const int nl = (int)h.nleaves;
-    FMM_TRY(h.c_tmp.reserve((size_t)(4 * nl + 2) * sizeof(unsigned)));
-    unsigned *cnt = h.c_tmp.as<unsigned>(), *off = cnt + nl, *tot = off + nl, *nrun = tot + 1;
+    FMM_TRY(h.c_tmp.reserve((size_t)(nl + 1) * sizeof(unsigned)));
+    unsigned *nrun = h.c_tmp.as<unsigned>();
     FMM_TRY(h.p2p_poff.reserve((size_t)(nl + 1) * sizeof(unsigned)));
     unsigned *roff = h.p2p_poff.as<unsigned>();
     // source runs of every target leaf's list
@@ -439,33 +412,25 @@ int build_p2p_items(Handle &h)
     k_p2p_runs<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
         nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.c_parent.as<int>(), h.c_pbeg.as<int>(),
         h.c_pcnt.as<int>(), h.c_geom.as<float4>(), roff, h.p2p_ent.as<float4>(), h.p2p_cnt.as<int>());
-    // work items
-    ++h.launches;
-    k_p2p_item_count<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pcnt.as<int>(), cnt);
-    FMM_TRY(scan_exclusive_u32(h, cnt, off, nl, tot));
-    FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
-    FMM_CUDA(cudaStreamSynchronize(h.stream));
-    h.n_items = h.pinned->level_total;
-    FMM_TRY(h.p2p_items.reserve(std::max<int64_t>(h.n_items, 1) * sizeof(int4)));
-    ++h.launches;
-    k_p2p_item_write<<<ceil_div(nl, 256), 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.c_pbeg.as<int>(),
-                                                              h.c_pcnt.as<int>(), off, h.p2p_items.as<int4>());
-    FMM_CHECK_LAUNCH("p2p items");
-    return FMM_OK;
+    FMM_CHECK_LAUNCH("p2p runs");
+    // work items (the adjoint's items are built on first use)
+    h.adj_items_ready = false;
+    return build_work_items(h, (h.flags & FMM_FLAG_KAHAN) ? kP2PGKahan : kP2PG, h.p2p_items, h.n_items);
 }
 
 template <int P, bool kKahan> static int p2p_launch(Handle &h, float *phi, float *grad)
 {
+    constexpr int G = kKahan ? kP2PGKahan : kP2PG;
     static bool configured[64] = {};
     if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
-        FMM_CUDA(cudaFuncSetAttribute(k_p2p<P, kKahan>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2PSmem));
+        FMM_CUDA(cudaFuncSetAttribute(k_p2p<P, kKahan, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2PSmem));
         configured[h.device] = true;
     }
     const float phi_scale = (float)(1.0 / h.norm_host[3]);
     const float grad_scale = (float)(1.0 / (h.norm_host[3] * h.norm_host[3]));
     const int blocks = ceil_div((int64_t)h.n_items * 32, kP2PThreads);
     ++h.launches;
-    k_p2p<P, kKahan><<<blocks, kP2PThreads, kP2PSmem, h.stream>>>(
+    k_p2p<P, kKahan, G><<<blocks, kP2PThreads, kP2PSmem, h.stream>>>(
         (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
         h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
         h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,

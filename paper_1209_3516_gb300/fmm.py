@@ -42,7 +42,7 @@ class _Stats(ctypes.Structure):
                 ("nlevels", ctypes.c_int32), ("P", ctypes.c_int32), ("n_m2l", ctypes.c_int64),
                 ("n_p2p", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_evaluate", ctypes.c_double), ("ms_phase", ctypes.c_double * len(PHASES)),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("ms_backward", ctypes.c_double)]
 
 
 _lib = None
@@ -134,6 +134,7 @@ class FMM:
         _check(L.fmm_create(ctypes.byref(h), int(N), int(P), float(theta), int(ncrit), ctypes.byref(opt)))
         self._h = h
         self.N, self.P, self.theta, self.ncrit = int(N), int(P), float(theta), int(ncrit)
+        self.evaluations = 0   # fmm_evaluate calls so far (the adjoint differentiates the last one)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -171,6 +172,7 @@ class FMM:
         pp = _dev_ptr(phi, torch.float32, (self.N,), "phi") if phi is not None else None
         gp = _dev_ptr(grad, torch.float32, (self.N, 3), "grad") if grad is not None else None
         _check(load().fmm_evaluate(self._h, xp, qp, pp, gp))
+        self.evaluations += 1
         return phi, grad
 
     def evaluate_host(self, x, q, phi=None, grad=None):
@@ -182,6 +184,7 @@ class FMM:
         if grad is None:
             grad = np.empty((self.N, 3), dtype=np.float32)
         _check(load().fmm_evaluate_host(self._h, _np_ptr(x), _np_ptr(q), _np_ptr(phi), _np_ptr(grad)))
+        self.evaluations += 1
         return phi, grad
 
     def energy(self) -> float:
@@ -189,8 +192,15 @@ class FMM:
         _check(load().fmm_energy(self._h, ctypes.byref(E)))
         return E.value
 
-    def backward(self, dphi=None, dgrad=None, dq=None, dx=None):
+    def backward(self, dphi=None, dgrad=None, dq=None, dx=None, want_dq=True, want_dx=True):
+        """fmm_backward: (dL/dq (N,), dL/dx (N, 3)) float32 CUDA tensors for the
+        upstream gradients dphi (N,) and dgrad (N, 3) of the last evaluate."""
         import torch
+        dev = torch.device("cuda", self.device)
+        if want_dq and dq is None:
+            dq = torch.empty(self.N, dtype=torch.float32, device=dev)
+        if want_dx and dx is None:
+            dx = torch.empty(self.N, 3, dtype=torch.float32, device=dev)
         pp = _dev_ptr(dphi, torch.float32, (self.N,), "dphi") if dphi is not None else None
         gp = _dev_ptr(dgrad, torch.float32, (self.N, 3), "dgrad") if dgrad is not None else None
         qp = _dev_ptr(dq, torch.float32, (self.N,), "dq") if dq is not None else None

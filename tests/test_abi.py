@@ -75,3 +75,10 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not forbidden.search(text), f
+
+
+def test_backward_argument_checks(lib):
+    lib.fmm_backward.argtypes = [ctypes.c_void_p] * 5
+    lib.fmm_last_error_string.restype = ctypes.c_char_p
+    assert lib.fmm_backward(None, None, None, None, None) == -1
+    assert b"null handle" in lib.fmm_last_error_string()

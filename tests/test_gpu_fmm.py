@@ -250,3 +250,70 @@ def test_full_size_uniform_1m(torch_cuda, P, theta):
         # the benchmark configuration meets the metric's 1e-4 relative error
         assert e_phi <= 1e-4 and e_grad <= 1e-4
     h.close()
+
+
+KAHAN_CASES = [
+    # N, P, theta, ncrit, kind ("p": Plummer with the equal charges 1/N of the adaptive workload)
+    (20000, 4, 0.4, 32, "p"),
+    (30000, 8, 0.4, 128, "p"),
+    (16384, 4, 0.4, 64, "u"),
+    (5001, 6, 0.45, 17, "u"),
+]
+
+
+@pytest.mark.parametrize("N,P,theta,ncrit,kind", KAHAN_CASES)
+def test_kahan_parity_with_oracle(torch_cuda, N, P, theta, ncrit, kind):
+    # compensated P2P accumulation (work items of <= 8 targets): same tree and
+    # lists, same tolerance against the oracle FMM
+    x, q = inputs.uniform_cube(N, 1309 + N) if kind == "u" else inputs.plummer(N, 1311 + N)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit, kahan=True)
+    ref = oracle.FMM(N, P, theta, ncrit).build(x)
+    check_structure(h, ref)
+    pr, gr = ref.evaluate(q32)
+    assert rel_l2(phi, pr) <= TOL, rel_l2(phi, pr)
+    assert rel_l2(grad, gr) <= TOL, rel_l2(grad, gr)
+    h.close()
+
+
+def test_kahan_reduces_accumulation_error(torch_cuda):
+    # theta = 0: every pair is P2P, so the result is the direct sum and its error
+    # is FP32 rounding only; with equal positive charges the long per-target sums
+    # are where plain accumulation loses digits, and compensation must not lose more
+    N = 32768
+    x, _ = inputs.uniform_cube(N, 1409)
+    q32 = np.full(N, np.float32(1.0 / N)).astype(np.float64)
+    pd, gd = oracle.direct(x, q32)
+    h0, p0, g0 = run_gpu(torch_cuda, x, q32, 4, 0.0, 64, kahan=False)
+    h1, p1, g1 = run_gpu(torch_cuda, x, q32, 4, 0.0, 64, kahan=True)
+    e0, e1 = rel_l2(p0, pd), rel_l2(p1, pd)
+    print("theta=0 N=%d: potential error plain %.3e, compensated %.3e" % (N, e0, e1))
+    assert e1 <= TOL and e0 <= TOL
+    assert e1 <= e0
+    assert rel_l2(g1, gd) <= TOL
+    h0.close()
+    h1.close()
+
+
+@pytest.mark.slow
+def test_full_size_plummer_4m_kahan(torch_cuda):
+    # the adaptive workload: N = 4,194,304 Plummer sphere, charges 1/N, P = 4,
+    # theta = 0.4, ncrit = 64, compensated P2P: tree and lists bit-exact,
+    # potential and gradient on a 4,096-target sample against the oracle FMM
+    N, P, theta, ncrit = 4194304, 4, 0.4, 64
+    x, q = inputs.plummer(N, inputs.SEED_BASE + 2)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit, kahan=True)
+    ref = oracle.FMM(N, P, theta, ncrit).build(x)
+    check_structure(h, ref)
+    t = inputs.sample_targets(N, 4096)
+    pr, gr = ref.evaluate(q32, t)
+    assert rel_l2(phi[t], pr) <= TOL
+    assert rel_l2(grad[t], gr) <= TOL
+    pd, gd = oracle.direct(x, q32, t)
+    E = h.energy()
+    st = h.stats()
+    print("Plummer N=4M P=4 theta=0.4: err vs direct phi %.2e grad %.2e; E %.9e; cells %d levels %d M2L %d "
+          "P2P %d pairs %d" % (rel_l2(phi[t], pd), rel_l2(grad[t], gd), E, st["ncells"], st["nlevels"],
+                               st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
+    h.close()

@@ -28,9 +28,10 @@ MUTANTS = [
     ("taylor_dropped_term", "if (j2 >= 0) s2 += b[j2];", ";", "test_oracle_expansions.py"),
     ("l2p_gradient_factor", "g[a] += L[t] * k[a] * orc_mpow(r, km);", "g[a] += L[t] * orc_mpow(r, km);",
      "test_oracle_expansions.py"),
-    ("p2m_offset_sign", "double d[3] = {y[3 * j] - X[0], y[3 * j + 1] - X[1], y[3 * j + 2] - X[2]};",
-     "double d[3] = {X[0] - y[3 * j], X[1] - y[3 * j + 1], X[2] - y[3 * j + 2]};",
-     "test_oracle_expansions.py"),
+    ("p2m_offset_sign", "double d[3] = {y[3 * j] - X[0], y[3 * j + 1] - X[1], y[3 * j + 2] - X[2]};\n"
+     "        for (int t = 0; t < mi->nterms; ++t)\n",
+     "double d[3] = {X[0] - y[3 * j], X[1] - y[3 * j + 1], X[2] - y[3 * j + 2]};\n"
+     "        for (int t = 0; t < mi->nterms; ++t)\n", "test_oracle_expansions.py"),
     ("p2p_gradient_sign", "gs[3 * i + 1] -= w * dy;", "gs[3 * i + 1] += w * dy;", "test_oracle_fmm.py"),
     ("direct_wrong_power", "double w = q[j] / (r2 * r);\n            gx -= w * dx;",
      "double w = q[j] / (r2 * r2);\n            gx -= w * dx;", "test_oracle_direct.py"),
