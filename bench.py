@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="all", choices=["all", "none", "adaptive", "differentiated"],
+                    help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
+                         "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
+    ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
     return ap.parse_args()
 
 
@@ -263,6 +267,98 @@ def run_reference(a):
     return 0
 
 
+def time_steps(torch, stream, fn, steps, warmup, flush):
+    """Mean device time (ms) of fn over `steps` calls, L2 flushed before each."""
+    for _ in range(warmup):
+        flush.fill_(1)
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(s.elapsed_time(e) for s, e in ev)
+
+
+def run_variants(torch, stream, flush, which="all"):
+    """The adaptive and the differentiated workloads, each against the plain FP32
+    path on the same GPU (same inputs, same step, only the variant switched)."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    out = {}
+    if which in ("all", "adaptive"):
+        out.update(variant_adaptive(torch, stream, flush))
+    if which in ("all", "differentiated"):
+        out.update(variant_differentiated(torch, stream, flush))
+    return out
+
+
+def variant_adaptive(torch, stream, flush):
+    from paper_1209_3516_gb300 import fmm, inputs
+    out = {}
+    # adaptive: N = 4,194,304 Plummer sphere, charges 1/N, P = 4, theta = 0.4, ncrit = 64
+    N, P, theta, ncrit = 4194304, 4, 0.4, 64
+    x, q = inputs.plummer(N, inputs.SEED_BASE + 2)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    phi = torch.empty(N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(N, 3, dtype=torch.float32, device="cuda")
+    res = {}
+    for kahan in (False, True):
+        h = fmm.FMM(N, P, theta, ncrit, kahan=kahan, timing=True)
+
+        def step():
+            h.build(xd)
+            h.evaluate(qd, phi=phi, grad=grad)
+        ms = time_steps(torch, stream, step, 5, 2, flush)
+        st = h.stats()
+        res[kahan] = (ms, st["ms_phase"]["p2p"], st["p2p_pairs"], st["ncells"], st["nlevels"])
+        h.close()
+    ms0, p0, pairs, ncells, nlev = res[False]
+    ms1, p1, _, _, _ = res[True]
+    out["adaptive_plummer_4m"] = {
+        "workload": "Plummer sphere N=4194304 (a=1, r<=100, charges 1/N), P=4, theta=0.4, ncrit=64, "
+                    "build + evaluate",
+        "evals_per_s": {"plain_fp32": 1e3 / ms0, "compensated_p2p": 1e3 / ms1},
+        "p2p_gpair_s": {"plain_fp32": pairs / (p0 * 1e-3) / 1e9, "compensated_p2p": pairs / (p1 * 1e-3) / 1e9},
+        "compensated_vs_plain": ms0 / ms1, "p2p_pairs": pairs, "ncells": ncells, "nlevels": nlev}
+    return out
+
+
+def variant_differentiated(torch, stream, flush):
+    from paper_1209_3516_gb300 import fmm, inputs
+    out = {}
+    # differentiated: N = 262,144 uniform cube, P = 6, theta = 0.4: forward + fmm_backward
+    N, P, theta, ncrit = 262144, 6, 0.4, 64
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 5)
+    g = inputs.rng(inputs.SEED_BASE + 6)
+    a = torch.from_numpy(g.standard_normal(N).astype(np.float32)).cuda()
+    b = torch.from_numpy(g.standard_normal((N, 3)).astype(np.float32)).cuda()
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    phi = torch.empty(N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(N, 3, dtype=torch.float32, device="cuda")
+    dq = torch.empty(N, dtype=torch.float32, device="cuda")
+    dx = torch.empty(N, 3, dtype=torch.float32, device="cuda")
+    h = fmm.FMM(N, P, theta, ncrit)
+    h.build(xd)
+    ms_f = time_steps(torch, stream, lambda: h.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)
+
+    def fwd_bwd():
+        h.evaluate(qd, phi=phi, grad=grad)
+        h.backward(a, b, dq=dq, dx=dx)
+    ms_fb = time_steps(torch, stream, fwd_bwd, 20, 3, flush)
+    h.close()
+    out["differentiated_262k"] = {
+        "workload": "uniform cube N=262144, P=6, theta=0.4, ncrit=64, tree built once; forward = fmm_evaluate, "
+                    "backward = fmm_backward(dphi, dgrad ~ N(0,1)) -> dq, dx",
+        "evals_per_s": {"forward": 1e3 / ms_f, "forward_plus_backward": 1e3 / ms_fb},
+        "ms": {"forward": ms_f, "backward": ms_fb - ms_f}, "backward_vs_forward": (ms_fb - ms_f) / ms_f}
+    return out
+
+
 def run_ours(a):
     import torch
     from paper_1209_3516_gb300 import fmm
@@ -367,6 +463,12 @@ def run_ours(a):
         if not a.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(a, x, q)
     h.close()
+    if line is not None and a.variants != "none" and ws == 1 and a.dist == "uniform":
+        try:
+            del xd, qd, phi, grad
+            line["variants"] = run_variants(torch, stream, flush, a.variants)
+        except Exception as e:   # a variant never hides the main line
+            line["variants"] = {"error": repr(e)[:300]}
     if line is not None:
         print(json.dumps(line))
     if pg is not None:
@@ -378,6 +480,12 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.variants_only:
+        import torch
+        torch.cuda.set_device(0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        print(json.dumps({"variants": run_variants(torch, torch.cuda.current_stream(), flush, a.variants)}))
+        return 0
     return run_ours(a)
 
 

@@ -21,7 +21,8 @@
 // the item's source runs are staged per warp in shared memory (positions,
 // adjoint sources and frame shifts; 128 particles per chunk, double-buffered
 // with cp.async); each lane takes one staged source and computes its pairs
-// with every target (34 FP32 operations and one SFU rsqrt per pair).  The
+// with every target (two targets per packed FP32 instruction: 16 issue slots
+// and one SFU rsqrt per pair).  The
 // 4 x 8 sums are reduce-scattered so that lane 4g + k owns component k of
 // target g, which then adds its far-field terms and writes the result.
 #include <cuda_runtime.h>
@@ -38,40 +39,60 @@ constexpr int kAdjThreads = 128;
 constexpr int kAdjSlots = 128;    // staged sources per buffer
 constexpr int kAdjSmem = (kAdjThreads / 32) * 2 * 3 * kAdjSlots * (int)sizeof(float4);   // 48 KiB
 
+// Per-target operands of the pair terms, two targets per float2 (packed FP32):
+// negated positions, q, a and negated b'.
+struct AdjTargets {
+    float2 nx[4], ny[4], nz[4], q[4], a[4], nbx[4], nby[4], nbz[4];
+};
+
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+
 // Pairs of one source (sp = position in the target frame and q, sa = (a, b'))
-// with NT targets (tp = position and q, ta = (a, b')).
+// with NT targets, two per packed FP32 instruction (FFMA2 / FADD2 / FMUL2):
+// 32 packed operations and two SFU rsqrt per two pairs.  acc[4 h + k] holds
+// component k (dq, dx, dy, dz) of targets 2h, 2h+1.
 template <int NT, bool kExact>
-__device__ __forceinline__ void adj_tile(const float4 &sp, const float4 &sa, const float4 *tp, const float4 *ta,
-                                         float *acc)
+__device__ __forceinline__ void adj_tile(const float4 &sp, const float4 &sa, const AdjTargets &t, float2 *acc)
 {
     constexpr float kEps = 1.17549435e-38f;   // FLT_MIN: keeps rsqrt finite, see the forward P2P
+    const float2 eps = bcast(kEps), m3 = bcast(-3.0f);
+    const float2 sx = bcast(sp.x), sy = bcast(sp.y), sz = bcast(sp.z), sq = bcast(sp.w);
+    const float2 sa2 = bcast(sa.x), sbx = bcast(sa.y), sby = bcast(sa.z), sbz = bcast(sa.w);
+    const float2 nsbx = bcast(-sa.y), nsby = bcast(-sa.z), nsbz = bcast(-sa.w);
 #pragma unroll
-    for (int g = 0; g < NT; ++g) {
-        const float ex = sp.x - tp[g].x, ey = sp.y - tp[g].y, ez = sp.z - tp[g].z;
-        const float r2 = fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, kEps)));
-        float rinv;
-        if (kExact) rinv = r2 > kEps ? rsqrt_approx(r2) : 0.0f;
-        else rinv = rsqrt_approx(r2);
-        const float rinv2 = rinv * rinv;
-        const float rinv3 = rinv2 * rinv;
-        const float bse = fmaf(sa.w, ez, fmaf(sa.z, ey, sa.y * ex));
-        acc[4 * g] = fmaf(-bse, rinv3, fmaf(sa.x, rinv, acc[4 * g]));
-        const float S = fmaf(tp[g].w, sa.x, ta[g].x * sp.w);
-        const float cx = fmaf(tp[g].w, sa.y, -sp.w * ta[g].y);
-        const float cy = fmaf(tp[g].w, sa.z, -sp.w * ta[g].z);
-        const float cz = fmaf(tp[g].w, sa.w, -sp.w * ta[g].w);
-        const float ce = fmaf(cz, ez, fmaf(cy, ey, cx * ex));
-        const float f = fmaf(-3.0f * ce, rinv2, S);
-        acc[4 * g + 1] = fmaf(fmaf(f, ex, cx), rinv3, acc[4 * g + 1]);
-        acc[4 * g + 2] = fmaf(fmaf(f, ey, cy), rinv3, acc[4 * g + 2]);
-        acc[4 * g + 3] = fmaf(fmaf(f, ez, cz), rinv3, acc[4 * g + 3]);
+    for (int h = 0; h < NT / 2; ++h) {
+        const float2 ex = __fadd2_rn(sx, t.nx[h]), ey = __fadd2_rn(sy, t.ny[h]), ez = __fadd2_rn(sz, t.nz[h]);
+        const float2 r2 = __ffma2_rn(ez, ez, __ffma2_rn(ey, ey, __ffma2_rn(ex, ex, eps)));
+        float2 rinv;
+        if (kExact) {
+            rinv.x = r2.x > kEps ? rsqrt_approx(r2.x) : 0.0f;
+            rinv.y = r2.y > kEps ? rsqrt_approx(r2.y) : 0.0f;
+        } else {
+            rinv.x = rsqrt_approx(r2.x);
+            rinv.y = rsqrt_approx(r2.y);
+        }
+        const float2 rinv2 = __fmul2_rn(rinv, rinv);
+        const float2 rinv3 = __fmul2_rn(rinv2, rinv);
+        // dq: a_s / r - (b'_s . e) / r^3
+        const float2 nbse = __ffma2_rn(nsbz, ez, __ffma2_rn(nsby, ey, __fmul2_rn(nsbx, ex)));
+        acc[4 * h] = __ffma2_rn(nbse, rinv3, __ffma2_rn(sa2, rinv, acc[4 * h]));
+        // dx: [C + (S - 3 (C . e) / r^2) e] / r^3
+        const float2 S = __ffma2_rn(t.q[h], sa2, __fmul2_rn(t.a[h], sq));
+        const float2 cx = __ffma2_rn(t.q[h], sbx, __fmul2_rn(sq, t.nbx[h]));
+        const float2 cy = __ffma2_rn(t.q[h], sby, __fmul2_rn(sq, t.nby[h]));
+        const float2 cz = __ffma2_rn(t.q[h], sbz, __fmul2_rn(sq, t.nbz[h]));
+        const float2 ce = __ffma2_rn(cz, ez, __ffma2_rn(cy, ey, __fmul2_rn(cx, ex)));
+        const float2 f = __ffma2_rn(ce, __fmul2_rn(rinv2, m3), S);
+        acc[4 * h + 1] = __ffma2_rn(__ffma2_rn(f, ex, cx), rinv3, acc[4 * h + 1]);
+        acc[4 * h + 2] = __ffma2_rn(__ffma2_rn(f, ey, cy), rinv3, acc[4 * h + 2]);
+        acc[4 * h + 3] = __ffma2_rn(__ffma2_rn(f, ez, cz), rinv3, acc[4 * h + 3]);
     }
 }
 
 template <int NT>
 __device__ __forceinline__ void adj_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
-                                           const float4 *adj, float4 *buf, int lb0, int lb1, const float4 *tp,
-                                           const float4 *ta, float *acc)
+                                           const float4 *adj, float4 *buf, int lb0, int lb1, const AdjTargets &t,
+                                           float2 *acc)
 {
     const int lane = (int)lane_id();
     // buffer b: [pos | adj | shift] x kAdjSlots at buf + b * 3 * kAdjSlots
@@ -101,8 +122,8 @@ __device__ __forceinline__ void adj_stream(RunCursor &cur, const float4 *run, co
                 sp.y += d.y;
                 sp.z += d.z;
             }
-            if (self_cur) adj_tile<NT, true>(sp, sa, tp, ta, acc);
-            else adj_tile<NT, false>(sp, sa, tp, ta, acc);
+            if (self_cur) adj_tile<NT, true>(sp, sa, t, acc);
+            else adj_tile<NT, false>(sp, sa, t, acc);
         }
         __syncwarp();   // every lane is done with this buffer before it is refilled
         n_cur = n_next;
@@ -146,19 +167,36 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
     const int leaf = it.x, tb = it.y, tc = it.z;
     const int lb0 = pbeg[leaf], lb1 = lb0 + pcnt[leaf];
 
-    float4 tp[kAdjG], ta[kAdjG];   // extra slots repeat the last target
+    AdjTargets t;   // extra slots repeat the last target
 #pragma unroll
-    for (int g = 0; g < kAdjG; ++g) {
-        tp[g] = pos[tb + min(g, tc - 1)];
-        ta[g] = adj[tb + min(g, tc - 1)];
+    for (int h = 0; h < kAdjG / 2; ++h) {
+        const int g0 = tb + min(2 * h, tc - 1), g1 = tb + min(2 * h + 1, tc - 1);
+        const float4 p0 = pos[g0], p1 = pos[g1], b0 = adj[g0], b1 = adj[g1];
+        t.nx[h] = make_float2(-p0.x, -p1.x);
+        t.ny[h] = make_float2(-p0.y, -p1.y);
+        t.nz[h] = make_float2(-p0.z, -p1.z);
+        t.q[h] = make_float2(p0.w, p1.w);
+        t.a[h] = make_float2(b0.x, b1.x);
+        t.nbx[h] = make_float2(-b0.y, -b1.y);
+        t.nby[h] = make_float2(-b0.z, -b1.z);
+        t.nbz[h] = make_float2(-b0.w, -b1.w);
     }
-    float acc[4 * kAdjG];
+    float2 a2[2 * kAdjG];
 #pragma unroll
-    for (int i = 0; i < 4 * kAdjG; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < 2 * kAdjG; ++i) a2[i] = make_float2(0.0f, 0.0f);
     RunCursor cur;
     cur.init(roff, it.w, run, run_end);
-    if (tc <= 4) adj_stream<4>(cur, run, run_end, pos, adj, buf, lb0, lb1, tp, ta, acc);
-    else adj_stream<kAdjG>(cur, run, run_end, pos, adj, buf, lb0, lb1, tp, ta, acc);
+    if (tc <= 4) adj_stream<4>(cur, run, run_end, pos, adj, buf, lb0, lb1, t, a2);
+    else adj_stream<kAdjG>(cur, run, run_end, pos, adj, buf, lb0, lb1, t, a2);
+    // acc[4 g + k]: component k of target g
+    float acc[4 * kAdjG];
+#pragma unroll
+    for (int h = 0; h < kAdjG / 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[4 * (2 * h) + k] = a2[4 * h + k].x;
+            acc[4 * (2 * h + 1) + k] = a2[4 * h + k].y;
+        }
 
     warp_reduce_scatter32(acc);
     const int g = (int)(lane >> 2), k = (int)(lane & 3u);

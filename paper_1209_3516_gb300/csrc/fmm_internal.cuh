@@ -66,8 +66,8 @@ struct DevBuf {
 struct TravCounters {
     unsigned long long n_m2l;     // pairs emitted to the M2L list
     unsigned long long n_p2p;     // pairs emitted to the P2P list
-    unsigned long long n_next;    // pairs pushed to the next frontier / spill list
-    unsigned long long seed_next; // work-stack kernel: next seed to claim
+    unsigned long long pass_count[9];   // work-stack passes: seeds of pass p (spills of pass p - 1)
+    unsigned long long pass_claim[8];   // work-stack pass p: next seed to claim
     unsigned long long p2p_pairs; // sum over P2P pairs of n_target * n_source
     unsigned int overflow;        // bit 0: m2l, bit 1: p2p, bit 2: frontier/spill
     unsigned int nleaves;         // leaves found by the leaf-list kernel

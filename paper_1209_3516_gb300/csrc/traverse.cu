@@ -11,9 +11,13 @@
 //      frontier holds about four pairs per resident warp of the device;
 //   2. a persistent kernel: each warp claims seeds with an atomic counter and
 //      runs the traversal below each seed depth first on a private stack in
-//      shared memory, four pairs (32 child pairs) per step.  A warp whose stack
-//      is full spills the pushes to global memory; spilled pairs seed another
-//      launch.  No warp ever waits on another.
+//      shared memory, four pairs (32 child pairs) per step, for at most
+//      kSeedBudget steps per seed; a warp whose budget runs out (or whose stack
+//      is full) spills its remaining pairs to global memory, and the spilled
+//      pairs seed another launch.  The budget keeps the launches balanced on
+//      adaptive trees, where a few seeds own most of the traversal (the core of
+//      a Plummer sphere): their subtrees are cut into pieces that every warp
+//      shares in the next launch.  No warp ever waits on another.
 // The emitted (target, source) pairs are then sorted by (target, source) so
 // that every target cell owns a contiguous, ordered run of sources.
 #include <cuda_runtime.h>
@@ -30,6 +34,16 @@ constexpr unsigned kOvM2L = 1u, kOvP2P = 2u, kOvNext = 4u;
 constexpr int kStackCap = 256;      // pairs per warp stack
 constexpr int kStackWarps = 8;      // warps per block of the work-stack kernel
 constexpr int kStackBlocksPerSM = 8;   // 64 resident warps per SM (16 KiB shared memory per block)
+#ifndef FMM_SEED_BUDGET
+#define FMM_SEED_BUDGET 128
+#endif
+#ifndef FMM_PASSES_PER_SYNC
+#define FMM_PASSES_PER_SYNC 2
+#endif
+constexpr int kSeedBudget = FMM_SEED_BUDGET;   // steps per claimed seed before the rest is handed on
+constexpr int kPassesPerSync = FMM_PASSES_PER_SYNC;   // work-stack passes back to back between host checks
+static_assert(kPassesPerSync >= 1 && kPassesPerSync <= 8, "pass counters");
+constexpr int kMaxStackPasses = 256;
 
 struct Cell {
     float4 g;   // centre, radius
@@ -70,6 +84,8 @@ struct TravArgs {
     unsigned long long p2p_cap;
     int2 *next;
     unsigned long long next_cap;
+    unsigned long long *n_next;   // count of pairs written to next (seeding round or work-stack pass)
+    unsigned long long *claim;    // work-stack pass: next seed to claim
     TravCounters *ctr;
 };
 
@@ -125,17 +141,31 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
     __shared__ int2 stack[kStackWarps][kStackCap];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     int2 *st = stack[w];
-    int top = 0;
+    int top = 0, steps = 0;
     for (;;) {
+        if (top > 0 && steps >= kSeedBudget) {
+            // budget used up: hand the remaining pairs to the next launch
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.n_next, (unsigned long long)top);
+            base = __shfl_sync(kFull, base, 0);
+            for (int i = (int)lane; i < top; i += 32) {
+                if (base + i < a.next_cap) a.next[base + i] = st[i];
+                else atomicOr(&a.ctr->overflow, kOvNext);
+            }
+            top = 0;
+            __syncwarp();
+        }
         if (top == 0) {
             unsigned long long s = 0;
-            if (lane == 0) s = atomicAdd(&a.ctr->seed_next, 1ull);
+            if (lane == 0) s = atomicAdd(a.claim, 1ull);
             s = __shfl_sync(kFull, s, 0);
             if (s >= nseeds) break;
             if (lane == 0) st[0] = seeds[s];
             top = 1;
+            steps = 0;
             __syncwarp();
         }
+        ++steps;
         const int npop = min(top, 4);
         top -= npop;
         const int p = (int)(lane >> 3), j = (int)(lane & 7u);
@@ -156,7 +186,7 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
             if (kind == 3) st[top + __popc(push & lanemask_lt())] = np;
             top += npush;
         } else {
-            warp_append(kind == 3, np, a.next, a.next_cap, &a.ctr->n_next, &a.ctr->overflow, kOvNext);
+            warp_append(kind == 3, np, a.next, a.next_cap, a.n_next, &a.ctr->overflow, kOvNext);
         }
         __syncwarp();
     }
@@ -309,6 +339,8 @@ int build_lists(Handle &h)
         a.p2p = h.p2p_raw.as<int2>();
         a.p2p_cap = h.p2p_cap;
         a.next_cap = h.front_cap;
+        a.n_next = nullptr;
+        a.claim = nullptr;
         a.ctr = ctr;
         if (h.nlevels <= 1) {
             // the root is a leaf: the single P2P pair (root, root)
@@ -336,14 +368,30 @@ int build_lists(Handle &h)
             cur ^= 1;
         }
         FMM_CHECK_LAUNCH("dtt rounds");
-        // 2. work-stack kernel on the last frontier, relaunched on spilled pairs
-        const unsigned long long *nseeds_dev = &ctr->round_count[nrounds];
+        // 2. work-stack passes on the last frontier: pass p claims the seeds counted
+        //    in pass_count[p] and spills into pass_count[p + 1]; kPassesPerSync
+        //    passes run back to back, then the host checks for spills left over
         bool overflow = false;
-        for (;;) {
-            a.next = h.front[cur ^ 1].as<int2>();
-            FMM_CUDA(cudaMemsetAsync(&ctr->n_next, 0, 2 * sizeof(unsigned long long), h.stream));   // n_next, seed_next
-            ++h.launches;
-            k_dtt_stack<<<stack_blocks, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(), nseeds_dev, a);
+        const unsigned long long *nseeds_dev = &ctr->round_count[nrounds];
+        for (int pass = 0;; pass += kPassesPerSync) {
+            if (pass >= kMaxStackPasses) {
+                set_error("dual tree traversal: work-stack pass limit reached");
+                return FMM_ERR_CAPACITY;
+            }
+            // seeds first (on later passes they sit in pass_count[kPassesPerSync]), then reset the rest
+            FMM_CUDA(cudaMemcpyAsync(&ctr->pass_count[0], nseeds_dev, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToDevice, h.stream));
+            FMM_CUDA(cudaMemsetAsync(&ctr->pass_claim[0], 0, sizeof(ctr->pass_claim), h.stream));
+            FMM_CUDA(cudaMemsetAsync(&ctr->pass_count[1], 0, kPassesPerSync * sizeof(unsigned long long), h.stream));
+            for (int p = 0; p < kPassesPerSync; ++p) {
+                a.next = h.front[cur ^ 1].as<int2>();
+                a.n_next = &ctr->pass_count[p + 1];
+                a.claim = &ctr->pass_claim[p];
+                ++h.launches;
+                k_dtt_stack<<<stack_blocks, kStackWarps * 32, 0, h.stream>>>(h.front[cur].as<int2>(),
+                                                                             &ctr->pass_count[p], a);
+                cur ^= 1;
+            }
             FMM_CHECK_LAUNCH("dtt stack");
             FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));
@@ -351,13 +399,8 @@ int build_lists(Handle &h)
                 overflow = true;
                 break;
             }
-            if (hc->n_next == 0) break;
-            nseeds_dev = &ctr->n_next;   // the spilled pairs seed the next launch
-            // the seed count must survive the reset of n_next: keep it in the last round slot
-            FMM_CUDA(cudaMemcpyAsync(&ctr->round_count[15], &ctr->n_next, sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToDevice, h.stream));
-            nseeds_dev = &ctr->round_count[15];
-            cur ^= 1;
+            if (hc->pass_count[kPassesPerSync] == 0) break;
+            nseeds_dev = &ctr->pass_count[kPassesPerSync];   // copied into pass_count[0] above
         }
         if (!overflow) {
             h.n_m2l = (int64_t)hc->n_m2l;
@@ -375,8 +418,9 @@ int build_lists(Handle &h)
         }
         // The traversal stopped at the first overflow, so the counters are lower
         // bounds: at least double what overflowed and run again.
-        unsigned long long max_round = hc->n_next;
+        unsigned long long max_round = 0;
         for (int r = 0; r <= nrounds; ++r) max_round = std::max(max_round, hc->round_count[r]);
+        for (int p = 0; p <= kPassesPerSync; ++p) max_round = std::max(max_round, hc->pass_count[p]);
         if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 3 / 2) + 1024);
         if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 3 / 2) + 1024);
         if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 2, (int64_t)(max_round * 3 / 2) + 4096);
