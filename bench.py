@@ -53,10 +53,11 @@ def parse():
     ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="all", choices=["all", "none", "adaptive", "differentiated"],
+    ap.add_argument("--variants", default="all", choices=["all", "none", "adaptive", "differentiated", "batched"],
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
+    ap.add_argument("--batch-n", type=int, default=1048576, help="N of the batched variant (a smaller case for ncu)")
     return ap.parse_args()
 
 
@@ -283,7 +284,7 @@ def time_steps(torch, stream, fn, steps, warmup, flush):
     return statistics.mean(s.elapsed_time(e) for s, e in ev)
 
 
-def run_variants(torch, stream, flush, which="all"):
+def run_variants(torch, stream, flush, which="all", batch_n=1048576):
     """The adaptive and the differentiated workloads, each against the plain FP32
     path on the same GPU (same inputs, same step, only the variant switched)."""
     from paper_1209_3516_gb300 import fmm, inputs
@@ -292,7 +293,42 @@ def run_variants(torch, stream, flush, which="all"):
         out.update(variant_adaptive(torch, stream, flush))
     if which in ("all", "differentiated"):
         out.update(variant_differentiated(torch, stream, flush))
+    if which in ("all", "batched"):
+        out.update(variant_batched(torch, stream, flush, batch_n))
     return out
+
+
+def variant_batched(torch, stream, flush, N=1048576):
+    """32 Gaussian charge vectors on the N = 1M uniform geometry (P = 8, theta = 0.5):
+    one fmm_evaluate_batch against 32 plain fmm_evaluate calls, tree built once."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    P, theta, ncrit, nrhs = 8, 0.5, 64, 32
+    x, _ = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    Q = torch.from_numpy(inputs.gaussian_charges(N, nrhs, inputs.SEED_BASE + 3).astype(np.float32)).cuda()
+    xd = torch.from_numpy(x).cuda()
+    phi = torch.empty(nrhs, N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(nrhs, N, 3, dtype=torch.float32, device="cuda")
+    h = fmm.FMM(N, P, theta, ncrit, timing=True)
+    h.build(xd)
+    ms_b = time_steps(torch, stream, lambda: h.evaluate_batch(Q, phi=phi, grad=grad), 5, 2, flush)
+    st_b = h.stats()
+    phases_b = {k: st_b["ms_phase"][k] for k in ("upward", "m2l", "downward", "p2p")}
+
+    def plain():
+        for r in range(nrhs):
+            h.evaluate(Q[r], phi=phi[r], grad=grad[r])
+    ms_p = time_steps(torch, stream, plain, 3, 1, flush)
+    pairs = h.stats()["p2p_pairs"]
+    h.close()
+    return {"batched_1m_32rhs": {
+        "workload": "uniform cube N=%d, 32 charge vectors ~ N(0,1), P=8, theta=0.5, ncrit=64, tree built " % N +
+                    "once; fmm_evaluate_batch (FP32 far field, P2P on tensor cores: BF16 hi/lo split, 3 MMAs, "
+                    "FP32 accumulate) vs 32 x fmm_evaluate (plain FP32)",
+        "vector_evals_per_s": {"plain_fp32": nrhs * 1e3 / ms_p, "batched": nrhs * 1e3 / ms_b},
+        "ms": {"plain_fp32_32x": ms_p, "batched": ms_b}, "batched_vs_plain": ms_p / ms_b,
+        "batched_phases_ms": phases_b,
+        "p2p_pair_vectors_per_s_batched": pairs * nrhs / (phases_b["p2p"] * 1e-3),
+        "p2p_pair_vectors_per_s_batched_lower_bound": pairs * nrhs / (ms_b * 1e-3)}}
 
 
 def variant_adaptive(torch, stream, flush):
@@ -466,7 +502,7 @@ def run_ours(a):
     if line is not None and a.variants != "none" and ws == 1 and a.dist == "uniform":
         try:
             del xd, qd, phi, grad
-            line["variants"] = run_variants(torch, stream, flush, a.variants)
+            line["variants"] = run_variants(torch, stream, flush, a.variants, a.batch_n)
         except Exception as e:   # a variant never hides the main line
             line["variants"] = {"error": repr(e)[:300]}
     if line is not None:
@@ -484,7 +520,8 @@ def main():
         import torch
         torch.cuda.set_device(0)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        print(json.dumps({"variants": run_variants(torch, torch.cuda.current_stream(), flush, a.variants)}))
+        print(json.dumps({"variants": run_variants(torch, torch.cuda.current_stream(), flush, a.variants,
+                                                   a.batch_n)}))
         return 0
     return run_ours(a)
 

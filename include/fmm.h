@@ -50,6 +50,9 @@ extern "C" {
 #define FMM_FLAG_KAHAN 1u         /* compensated (Kahan) P2P accumulation per target */
 #define FMM_FLAG_TIMING 2u        /* record per-phase device times (adds events) */
 
+/* Largest number of charge vectors of one fmm_evaluate_batch call. */
+#define FMM_MAX_RHS 32
+
 typedef struct fmm_handle fmm_handle;
 
 typedef struct fmm_options {
@@ -84,6 +87,7 @@ struct fmm_stats {
     double ms_phase[FMM_NPHASES];          /* per phase, when FMM_FLAG_TIMING is set */
     int64_t kernel_launches;               /* CUDA kernels launched by this handle since creation */
     double ms_backward;                    /* device time of the last fmm_backward */
+    double ms_batch;                       /* device time of the last fmm_evaluate_batch */
 };
 
 /*
@@ -129,6 +133,25 @@ int fmm_build(fmm_handle *h, const double *x);
  * Asynchronous on the handle's stream.
  */
 int fmm_evaluate(fmm_handle *h, const double *x, const float *q, float *phi, float *grad);
+
+/*
+ * fmm_evaluate_batch -- potentials and gradients of nrhs charge vectors on one
+ * geometry in one call (the many-right-hand-side form of fmm_evaluate).
+ *   x     as in fmm_evaluate (rebuild if it differs from the last build; NULL reuses it).
+ *   q     device, nrhs x N FP32: vector r at q + r * N (caller order).
+ *   nrhs  1 <= nrhs <= FMM_MAX_RHS.
+ *   phi   out, device, nrhs x N FP32 (vector r at phi + r * N), or NULL.
+ *   grad  out, device, nrhs x N x 3 FP32 (vector r at grad + 3 r N), or NULL.
+ * The same tree, lists and operators as fmm_evaluate, with every operator a
+ * contraction over the vectors: P2M, M2M, M2L and L2L apply each geometric
+ * factor to all vectors (FP32); the P2P is a dense product on the tensor cores,
+ * Phi = G Q over 16-source tiles, with the kernel matrices G (1/r and e/r^3)
+ * generated in FP32 and G and Q each split into BF16 high and low parts (three
+ * MMAs, FP32 accumulation: about 2^-16 relative per term); L2P and the scatter
+ * are fused.  Asynchronous (the first call after a build synchronises once to
+ * size its work items).
+ */
+int fmm_evaluate_batch(fmm_handle *h, const double *x, const float *q, int nrhs, float *phi, float *grad);
 
 /*
  * fmm_evaluate_host -- fmm_build + fmm_evaluate on HOST arrays: copies x (N x 3

@@ -97,6 +97,7 @@ static int do_build(Handle &h, const double *x)
     h.built = false;
     h.evaluated = false;
     h.backward_done = false;
+    h.batch_done = false;
     const int ev0 = 2 * kPhases, ev1 = 2 * kPhases + 1;
     if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
     FMM_TRY(build_keys(h, x));
@@ -243,6 +244,31 @@ int fmm_evaluate(fmm_handle *w, const double *x, const float *q, float *phi, flo
     return do_evaluate(h, q, phi, grad);
 }
 
+int fmm_evaluate_batch(fmm_handle *w, const double *x, const float *q, int nrhs, float *phi, float *grad)
+{
+    if (!w || !q || (!phi && !grad)) {
+        set_error("fmm_evaluate_batch: null argument");
+        return FMM_ERR_ARG;
+    }
+    if (nrhs < 1 || nrhs > FMM_MAX_RHS) {
+        set_error("fmm_evaluate_batch: nrhs must be in [1, FMM_MAX_RHS]");
+        return FMM_ERR_ARG;
+    }
+    Handle &h = w->h;
+    DeviceGuard guard(h.device);
+    if (x && (!h.built || x != h.x_built)) FMM_TRY(do_build(h, x));
+    if (!h.built) {
+        set_error("fmm_evaluate_batch: no tree (call fmm_build or pass x)");
+        return FMM_ERR_STATE;
+    }
+    const int ev0 = 2 * kPhases + 6, ev1 = 2 * kPhases + 7;
+    if (h.events_ready) cudaEventRecord(h.ev[ev0], h.stream);
+    FMM_TRY(evaluate_batch(h, q, nrhs, phi, grad));
+    if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
+    h.batch_done = true;
+    return FMM_OK;
+}
+
 int fmm_evaluate_host(fmm_handle *w, const double *x_host, const float *q_host, float *phi_host, float *grad_host)
 {
     if (!w || !x_host || !q_host || (!phi_host && !grad_host)) {
@@ -342,6 +368,8 @@ int fmm_stats(fmm_handle *w, struct fmm_stats *s)
             s->ms_evaluate = ms;
         if (h.backward_done && cudaEventElapsedTime(&ms, h.ev[2 * kPhases + 4], h.ev[2 * kPhases + 5]) == cudaSuccess)
             s->ms_backward = ms;
+        if (h.batch_done && cudaEventElapsedTime(&ms, h.ev[2 * kPhases + 6], h.ev[2 * kPhases + 7]) == cudaSuccess)
+            s->ms_batch = ms;
         if (h.flags & FMM_FLAG_TIMING)
             for (int p = 0; p < kPhases; ++p) {
                 ms = 0.f;

@@ -154,6 +154,15 @@ struct Handle {
     int64_t n_adj_items = 0;
     bool adj_items_ready = false;
 
+    // many charge vectors (fmm_evaluate_batch): charges [N][32] in sorted order
+    // (FP32 and its BF16 hi / lo split), expansions [ncells][TP][32], work items
+    // of <= 8 targets
+    DevBuf qb, qbh, qbl;
+    DevBuf Mb, Lb;
+    DevBuf batch_items;
+    int64_t n_batch_items = 0;
+    bool batch_items_ready = false;
+
     DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
     DevBuf energy_part;   // double partials
 
@@ -164,11 +173,12 @@ struct Handle {
     int64_t launches = 0;
 
     // timing
-    cudaEvent_t ev[2 * kPhases + 6] = {};   // phases, build, evaluate, backward
+    cudaEvent_t ev[2 * kPhases + 8] = {};   // phases, build, evaluate, backward, batch
     bool events_ready = false;
     float ms_phase[kPhases] = {};
     float ms_build = 0.f, ms_eval = 0.f;
     bool backward_done = false;
+    bool batch_done = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -192,6 +202,7 @@ int evaluate_m2l(Handle &h, const float *M, float *L);
 int evaluate_downward(Handle &h, float *L);       // L2L
 int adjoint_upward(Handle &h, const float *dphi, const float *dgrad);   // gather (a, b / h), P2M, M2M into Ma
 int adjoint_p2p(Handle &h, float *dq, float *dx); // adjoint P2P + L2P terms + scatter
+int evaluate_batch(Handle &h, const float *q, int nrhs, float *phi, float *grad);   // many charge vectors
 int evaluate_p2p(Handle &h, float *phi, float *grad);   // P2P + L2P + scatter
 int energy_reduce(Handle &h, double *E);
 

@@ -42,7 +42,10 @@ class _Stats(ctypes.Structure):
                 ("nlevels", ctypes.c_int32), ("P", ctypes.c_int32), ("n_m2l", ctypes.c_int64),
                 ("n_p2p", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_evaluate", ctypes.c_double), ("ms_phase", ctypes.c_double * len(PHASES)),
-                ("kernel_launches", ctypes.c_int64), ("ms_backward", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_int64), ("ms_backward", ctypes.c_double),
+                ("ms_batch", ctypes.c_double)]
+
+MAX_RHS = 32
 
 
 _lib = None
@@ -69,6 +72,7 @@ def load():
     L.fmm_build.argtypes = [_vp, _vp]
     L.fmm_evaluate.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.fmm_evaluate_host.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.fmm_evaluate_batch.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
     L.fmm_energy.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     L.fmm_backward.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.fmm_stats.argtypes = [_vp, ctypes.POINTER(_Stats)]
@@ -173,6 +177,24 @@ class FMM:
         gp = _dev_ptr(grad, torch.float32, (self.N, 3), "grad") if grad is not None else None
         _check(load().fmm_evaluate(self._h, xp, qp, pp, gp))
         self.evaluations += 1
+        return phi, grad
+
+    def evaluate_batch(self, q, x=None, phi=None, grad=None, want_phi=True, want_grad=True):
+        """fmm_evaluate_batch: q (nrhs, N) float32 CUDA -> phi (nrhs, N), grad (nrhs, N, 3)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if q.dim() != 2:
+            raise ValueError("q must be (nrhs, N)")
+        nrhs = q.shape[0]
+        qp = _dev_ptr(q, torch.float32, (nrhs, self.N), "q")
+        xp = _dev_ptr(x, torch.float64, (self.N, 3), "x") if x is not None else None
+        if want_phi and phi is None:
+            phi = torch.empty(nrhs, self.N, dtype=torch.float32, device=dev)
+        if want_grad and grad is None:
+            grad = torch.empty(nrhs, self.N, 3, dtype=torch.float32, device=dev)
+        pp = _dev_ptr(phi, torch.float32, (nrhs, self.N), "phi") if phi is not None else None
+        gp = _dev_ptr(grad, torch.float32, (nrhs, self.N, 3), "grad") if grad is not None else None
+        _check(load().fmm_evaluate_batch(self._h, xp, qp, int(nrhs), pp, gp))
         return phi, grad
 
     def evaluate_host(self, x, q, phi=None, grad=None):
