@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="all", choices=["all", "none", "adaptive", "differentiated", "batched"],
+    ap.add_argument("--variants", default="all",
+                    choices=["all", "none", "adaptive", "differentiated", "batched", "systems"],
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
@@ -295,7 +296,56 @@ def run_variants(torch, stream, flush, which="all", batch_n=1048576):
         out.update(variant_differentiated(torch, stream, flush))
     if which in ("all", "batched"):
         out.update(variant_batched(torch, stream, flush, batch_n))
+    if which in ("all", "systems"):
+        out.update(variant_systems(torch, stream, flush))
     return out
+
+
+def variant_systems(torch, stream, flush):
+    """64 systems, N lognormal in [1000, 200000] (uniform cube, charges U[-1,1)),
+    P = 8, theta = 0.5: the merged evaluation replayed from one CUDA graph against
+    64 plain fmm_evaluate calls on per-system handles (trees built once)."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    P, theta, ncrit = 8, 0.5, 64
+    sizes = [int(n) for n in inputs.lognormal_sizes(64)]
+    xs, qs = [], []
+    for k, n in enumerate(sizes):
+        x, q = inputs.uniform_cube(n, inputs.SEED_BASE + 10 + k)
+        xs.append(x)
+        qs.append(q.astype(np.float32))
+    xd = torch.from_numpy(np.concatenate(xs)).cuda()
+    qd = torch.from_numpy(np.concatenate(qs)).cuda()
+    Ntot = sum(sizes)
+    phi = torch.empty(Ntot, dtype=torch.float32, device="cuda")
+    grad = torch.empty(Ntot, 3, dtype=torch.float32, device="cuda")
+    m = fmm.MultiFMM(sizes, P, theta, ncrit)
+    m.build(xd)
+    ms_m = time_steps(torch, stream, lambda: m.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)
+    info = m.info()
+    m.close()
+    hs, offs, off = [], [], 0
+    for n in sizes:
+        h = fmm.FMM(n, P, theta, ncrit)
+        h.build(xd[off:off + n])
+        hs.append(h)
+        offs.append(off)
+        off += n
+
+    def plain():
+        for h, o, n in zip(hs, offs, sizes):
+            h.evaluate(qd[o:o + n], phi=phi[o:o + n], grad=grad[o:o + n])
+    ms_p = time_steps(torch, stream, plain, 5, 2, flush)
+    for h in hs:
+        h.close()
+    return {"systems_64_lognormal": {
+        "workload": "64 systems, N ~ lognormal in [1000, 200000] (total %d), uniform cube, charges U[-1,1), "
+                    "P=8, theta=0.5, ncrit=64, trees built once; merged evaluation (one launch per operator) "
+                    "replayed from a CUDA graph vs 64 plain fmm_evaluate calls" % Ntot,
+        "system_sets_per_s": {"plain_fp32_64_calls": 1e3 / ms_p, "merged_graph": 1e3 / ms_m},
+        "ms": {"plain_fp32_64_calls": ms_p, "merged_graph": ms_m}, "merged_vs_plain": ms_p / ms_m,
+        "graph_nodes": info["graph_nodes"], "p2p_targets_per_item": info["p2p_targets_per_item"],
+        "autotune_p2p_ms": {"16_targets": info["tune_ms"][0], "8_targets": info["tune_ms"][1]},
+        "p2p_pairs": info["p2p_pairs"]}}
 
 
 def variant_batched(torch, stream, flush, N=1048576):

@@ -211,6 +211,58 @@ int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq
  */
 int fmm_energy_noalloc(const float *q, const float *phi, int64_t n, double *E, void *stream);
 
+/*
+ * Many independent systems in one evaluation.  Each system gets its own tree,
+ * normalisation and lists; fmm_multi_build merges them into one set of
+ * arrays (cells in (level, system) order, every index moved by its system's
+ * offset, a per-cell unit scale), so that each evaluation operator runs as one
+ * launch over all systems: one charge gather, one P2M, one M2M and one L2L per
+ * level, one M2L and one P2P.  fmm_multi_evaluate captures that evaluation into
+ * a CUDA graph on first use (after an eager run that sizes the buffers and an
+ * autotuner that times the P2P kernel with 16- and 8-target work items on the
+ * merged problem and keeps the faster) and replays the graph afterwards; new
+ * q / phi / grad pointers trigger a new capture.
+ */
+typedef struct fmm_multi fmm_multi;
+
+struct fmm_multi_info {
+    int64_t n_total;               /* particles over all systems */
+    int64_t ncells, nleaves;       /* merged cells and leaves */
+    int64_t n_m2l, p2p_pairs;      /* M2L cell pairs, P2P particle pairs over all systems */
+    int64_t graph_nodes;           /* kernel nodes of the captured evaluation */
+    int64_t kernel_launches;       /* kernels launched on the merged problem (merge, tuning, eager runs) */
+    int32_t nsys, nlevels;
+    int32_t p2p_targets_per_item;  /* the autotuner's choice */
+    int32_t reserved;
+    double tune_ms[2];             /* P2P kernel time with 16 and with 8 targets per item */
+    double ms_evaluate;            /* device time of the last graph replay */
+};
+
+/*
+ * fmm_multi_create -- nsys systems of N[s] particles (N: HOST array of nsys
+ * sizes, each >= 1, total < 2^31), one P, theta, ncrit for all.  opt may be
+ * NULL; opt->stream is the stream the calls are ordered after (the work runs
+ * on a private stream of the handle); Kahan and timing flags are ignored.
+ */
+int fmm_multi_create(fmm_multi **m, int nsys, const int64_t *N, int P, float theta, int ncrit,
+                     const fmm_options *opt);
+
+/* fmm_multi_build -- x: device, (sum N) x 3 FP64, the systems back to back.  Synchronous. */
+int fmm_multi_build(fmm_multi *m, const double *x);
+
+/*
+ * fmm_multi_evaluate -- q (device, sum N FP32, systems back to back) -> phi
+ * (sum N) and grad ((sum N) x 3), either may be NULL but not both; each
+ * system's particles interact only with each other.  Asynchronous with respect
+ * to the host (ordered after and before the caller's stream).
+ */
+int fmm_multi_evaluate(fmm_multi *m, const float *q, float *phi, float *grad);
+
+/* fmm_multi_info -- sizes, the autotuner's timings and choice, the last replay's time (HOST *info). */
+int fmm_multi_info(fmm_multi *m, struct fmm_multi_info *info);
+
+int fmm_multi_destroy(fmm_multi *m);
+
 /* fmm_stats -- counters and timings of the last build/evaluate into *s (HOST). */
 int fmm_stats(fmm_handle *h, struct fmm_stats *s);
 

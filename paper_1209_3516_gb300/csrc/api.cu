@@ -209,7 +209,9 @@ int fmm_destroy(fmm_handle *w)
                       &h.c_cbeg, &h.c_ccnt, &h.c_parent, &h.c_geom, &h.c_kids, &h.c_r2bits, &h.c_tmp, &h.leaf_of,
                       &h.counters, &h.front[0], &h.front[1], &h.m2l_raw, &h.p2p_raw, &h.lkeys, &h.lkeys_alt,
                       &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_poff, &h.p2p_ent, &h.p2p_cnt,
-                      &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad};
+                      &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad,
+                      &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb, &h.batch_items,
+                      &h.c_scale};
     for (DevBuf *b : bufs) b->release();
     if (h.events_ready)
         for (auto &ev : h.ev) cudaEventDestroy(ev);

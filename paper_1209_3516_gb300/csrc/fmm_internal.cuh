@@ -118,6 +118,7 @@ struct Handle {
     DevBuf c_prefix;      // u64
     DevBuf c_level, c_pbeg, c_pcnt, c_cbeg, c_ccnt, c_parent;   // int32
     DevBuf c_geom;        // float4 (centre, radius)
+    DevBuf c_scale;       // float2 (1/h, 1/h^2) per cell: output units when cells of several systems share arrays
     DevBuf c_kids;        // int2 (first child, child count) for the traversal
     DevBuf c_r2bits;      // u32 max squared radius (bits) during the build
     DevBuf c_tmp;         // int32 per-cell scratch (child counts / offsets)
@@ -141,6 +142,7 @@ struct Handle {
     DevBuf p2p_cnt;            // int end particle (exclusive) per source run
     int64_t n_pieces = 0;      // source runs over all target leaves
     int64_t n_items = 0;
+    int p2p_g = 0;             // targets per P2P work item (0: the default, 16; 8 on request)
     DevBuf pairs_count;        // u64 scratch (P2P particle-pair count)
 
     // expansions and outputs

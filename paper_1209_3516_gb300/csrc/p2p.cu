@@ -254,8 +254,9 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
                                                      const float4 *run, const int *run_end, const float4 *pos,
                                                      const int *pbeg, const int *pcnt, const int *level,
                                                      const int *parent, const float4 *geom, const float *L,
-                                                     const int *perm, float phi_scale, float grad_scale, float *phi,
-                                                     float *grad, float *phi_sorted)
+                                                     const int *perm, float phi_scale, float grad_scale,
+                                                     const float2 *cell_scale, float *phi, float *grad,
+                                                     float *phi_sorted)
 {
     static_assert(G % 4 == 0 && G <= 16, "targets per item");
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
@@ -359,6 +360,11 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
         gy = fmaf(ly, inv_s, gy);
         gz = fmaf(lz, inv_s, gz);
     }
+    if (cell_scale) {   // cells of several systems: each leaf carries its system's units
+        const float2 cs = cell_scale[leaf];
+        phi_scale = cs.x;
+        grad_scale = cs.y;
+    }
     const int dst = perm[sidx];
     const float ph = pot * phi_scale;
     if (phi) phi[dst] = ph;
@@ -416,12 +422,12 @@ int build_p2p_items(Handle &h)
     // work items (the adjoint's items are built on first use)
     h.adj_items_ready = false;
     h.batch_items_ready = false;
+    h.p2p_g = 0;
     return build_work_items(h, (h.flags & FMM_FLAG_KAHAN) ? kP2PGKahan : kP2PG, h.p2p_items, h.n_items);
 }
 
-template <int P, bool kKahan> static int p2p_launch(Handle &h, float *phi, float *grad)
+template <int P, bool kKahan, int G> static int p2p_launch(Handle &h, float *phi, float *grad)
 {
-    constexpr int G = kKahan ? kP2PGKahan : kP2PG;
     static bool configured[64] = {};
     if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
         FMM_CUDA(cudaFuncSetAttribute(k_p2p<P, kKahan, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2PSmem));
@@ -434,16 +440,19 @@ template <int P, bool kKahan> static int p2p_launch(Handle &h, float *phi, float
     k_p2p<P, kKahan, G><<<blocks, kP2PThreads, kP2PSmem, h.stream>>>(
         (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
         h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
-        h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale, phi,
-        grad, h.phi_sorted.as<float>());
+        h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale,
+        h.c_scale.as<float2>(), phi, grad, h.phi_sorted.as<float>());
     FMM_CHECK_LAUNCH("p2p");
     return FMM_OK;
 }
 
+// The work items must have been built with the matching target count
+// (kP2PGKahan with FMM_FLAG_KAHAN, else h.p2p_g or kP2PG).
 template <int P> static int p2p_impl(Handle &h, float *phi, float *grad)
 {
-    if (h.flags & FMM_FLAG_KAHAN) return p2p_launch<P, true>(h, phi, grad);
-    return p2p_launch<P, false>(h, phi, grad);
+    if (h.flags & FMM_FLAG_KAHAN) return p2p_launch<P, true, kP2PGKahan>(h, phi, grad);
+    if (h.p2p_g == 8) return p2p_launch<P, false, 8>(h, phi, grad);
+    return p2p_launch<P, false, kP2PG>(h, phi, grad);
 }
 
 int evaluate_p2p(Handle &h, float *phi, float *grad)

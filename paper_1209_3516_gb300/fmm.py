@@ -48,6 +48,14 @@ class _Stats(ctypes.Structure):
 MAX_RHS = 32
 
 
+class _MultiInfo(ctypes.Structure):
+    _fields_ = [("n_total", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("n_m2l", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("nsys", ctypes.c_int32), ("nlevels", ctypes.c_int32),
+                ("p2p_targets_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * 2), ("ms_evaluate", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -83,6 +91,12 @@ def load():
     L.fmm_get_cells.argtypes = [_vp] + [_vp] * 8
     L.fmm_get_lists.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _vp, _vp]
     L.fmm_energy_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+    L.fmm_multi_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                   ctypes.c_float, ctypes.c_int, ctypes.POINTER(_Options)]
+    L.fmm_multi_build.argtypes = [_vp, _vp]
+    L.fmm_multi_evaluate.argtypes = [_vp, _vp, _vp, _vp]
+    L.fmm_multi_info.argtypes = [_vp, ctypes.POINTER(_MultiInfo)]
+    L.fmm_multi_destroy.argtypes = [_vp]
     _lib = L
     return L
 
@@ -276,3 +290,60 @@ class FMM:
         p = np.zeros((npp.value, 2), dtype=np.int32)
         _check(load().fmm_get_lists(self._h, None, None, _np_ptr(m), _np_ptr(p)))
         return m, p
+
+
+class MultiFMM:
+    """fmm_multi_*: many independent systems (sizes N[s]) evaluated as one merged
+    problem, replayed from a CUDA graph."""
+
+    def __init__(self, sizes, P=4, theta=0.4, ncrit=64, stream=None, device=None):
+        import torch
+        L = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream, self.device = stream, int(device)
+        self.sizes = [int(n) for n in sizes]
+        self.N = sum(self.sizes)
+        arr = (ctypes.c_int64 * len(self.sizes))(*self.sizes)
+        opt = _Options(ctypes.c_void_p(stream.cuda_stream), self.device, 0)
+        h = _vp()
+        _check(L.fmm_multi_create(ctypes.byref(h), len(self.sizes), arr, int(P), float(theta), int(ncrit),
+                                  ctypes.byref(opt)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fmm_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, x):
+        import torch
+        _check(load().fmm_multi_build(self._h, _dev_ptr(x, torch.float64, (self.N, 3), "x")))
+        return self
+
+    def evaluate(self, q, phi=None, grad=None):
+        import torch
+        dev = torch.device("cuda", self.device)
+        qp = _dev_ptr(q, torch.float32, (self.N,), "q")
+        if phi is None:
+            phi = torch.empty(self.N, dtype=torch.float32, device=dev)
+        if grad is None:
+            grad = torch.empty(self.N, 3, dtype=torch.float32, device=dev)
+        _check(load().fmm_multi_evaluate(self._h, qp, _dev_ptr(phi, torch.float32, (self.N,), "phi"),
+                                         _dev_ptr(grad, torch.float32, (self.N, 3), "grad")))
+        return phi, grad
+
+    def info(self) -> dict:
+        i = _MultiInfo()
+        _check(load().fmm_multi_info(self._h, ctypes.byref(i)))
+        d = {k: getattr(i, k) for k, _ in _MultiInfo._fields_ if k not in ("tune_ms", "reserved")}
+        d["tune_ms"] = [i.tune_ms[0], i.tune_ms[1]]
+        return d
