@@ -509,6 +509,11 @@ def run_ours(a):
     achieved = pairs * FLOPS_PER_PAIR / (p2p_mean * 1e-3) / 1e12
     traffic = p2p_traffic(a)
 
+    # fmm_evaluate alone on the built tree (the paper's and the survey's
+    # "FMM evals/s": tree construction excluded); reported beside the build +
+    # evaluate step of `value`
+    ms_eval_only = time_steps(torch, stream, lambda: h.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)
+
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if a.e2e_steps > 0:
@@ -540,6 +545,8 @@ def run_ours(a):
                              "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
                              "launch_ms": p2p_mean,
                              "peak_basis": "%d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % (sms, sm_max)},
+                "evaluate_only": {"evals_per_s": 1e3 / ms_eval_only, "ms": ms_eval_only,
+                                  "particles_per_s": a.N * 1e3 / ms_eval_only},
                 "phases_ms": {k: statistics.mean(v) for k, v in phase_acc.items()},
                 "counts": {"ncells": st["ncells"], "nleaves": st["nleaves"], "nlevels": st["nlevels"],
                            "n_m2l": st["n_m2l"], "n_p2p": st["n_p2p"], "p2p_pairs": pairs},

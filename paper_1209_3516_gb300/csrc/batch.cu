@@ -369,41 +369,66 @@ __device__ __forceinline__ int batch_stage(RunCursor &cur, const float4 *run, co
     return padded;
 }
 
-// Kernel values of target (tx, ty, tz) and one staged source j: 1/r, e/r^3.
+// Kernel values of one target (ntx, nty, ntz: negated) with the two staged
+// sources j and j + 1 (positions already moved into the target frame), packed
+// FP32 (two pairs per instruction): 1/r and e/r^3, e = u_s - u_t, each as
+// (source j, source j + 1).
 template <bool kExact>
-__device__ __forceinline__ float4 kernel_values(const BatchBuf &b, int j, float tx, float ty, float tz)
+__device__ __forceinline__ void kernel_values2(const BatchBuf &b, int j, float2 ntx, float2 nty, float2 ntz,
+                                               float2 &k1, float2 &kx, float2 &ky, float2 &kz)
 {
     constexpr float kEps = 1.17549435e-38f;
-    float4 s = b.pos[j];
-    const float4 d = b.shift[j];
-    const float ex = s.x + d.x - tx, ey = s.y + d.y - ty, ez = s.z + d.z - tz;
-    const float r2 = fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, kEps)));
-    const float rinv = kExact ? (r2 > kEps ? rsqrt_approx(r2) : 0.0f) : rsqrt_approx(r2);
-    const float rinv3 = rinv * rinv * rinv;
-    return make_float4(rinv, ex * rinv3, ey * rinv3, ez * rinv3);
+    const float4 s0 = b.pos[j], s1 = b.pos[j + 1];
+    const float2 ex = __fadd2_rn(make_float2(s0.x, s1.x), ntx);
+    const float2 ey = __fadd2_rn(make_float2(s0.y, s1.y), nty);
+    const float2 ez = __fadd2_rn(make_float2(s0.z, s1.z), ntz);
+    const float2 r2 = __ffma2_rn(ez, ez, __ffma2_rn(ey, ey, __ffma2_rn(ex, ex, make_float2(kEps, kEps))));
+    float2 rinv;
+    if (kExact) {
+        rinv.x = r2.x > kEps ? rsqrt_approx(r2.x) : 0.0f;
+        rinv.y = r2.y > kEps ? rsqrt_approx(r2.y) : 0.0f;
+    } else {
+        rinv.x = rsqrt_approx(r2.x);
+        rinv.y = rsqrt_approx(r2.y);
+    }
+    const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+    k1 = rinv;
+    kx = __fmul2_rn(ex, rinv3);
+    ky = __fmul2_rn(ey, rinv3);
+    kz = __fmul2_rn(ez, rinv3);
+}
+
+// v = hi + lo for a pair of values: hi = bf16(v), lo = bf16(v - hi), packed
+// two per register (lower half: the first value)
+__device__ __forceinline__ void split_bf16x2(float2 v, unsigned &hi, unsigned &lo)
+{
+    hi = pack_bf16(v.x, v.y);
+    const float2 hf = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+    const float2 r = __fadd2_rn(v, make_float2(-hf.x, -hf.y));
+    lo = pack_bf16(r.x, r.y);
 }
 
 // One k16 step: 16 staged sources from k0.  Thread (g = lane / 4, t = lane % 4)
 // computes target g with sources k0 + {2t, 2t+1, 2t+8, 2t+9}: the A fragments
 // of two m16 tiles (rows g / g+8: phi / gx in tile 0, gy / gz in tile 1).
 template <bool kExact>
-__device__ __forceinline__ void batch_kstep(const BatchBuf &b, int k0, float tx, float ty, float tz, float (*acc)[4][4])
+__device__ __forceinline__ void batch_kstep(const BatchBuf &b, int k0, float2 ntx, float2 nty, float2 ntz,
+                                            float (*acc)[4][4])
 {
     const int lane = (int)lane_id();
     const int t = lane & 3;
-    const float4 v0 = kernel_values<kExact>(b, k0 + 2 * t, tx, ty, tz);
-    const float4 v1 = kernel_values<kExact>(b, k0 + 2 * t + 1, tx, ty, tz);
-    const float4 v8 = kernel_values<kExact>(b, k0 + 2 * t + 8, tx, ty, tz);
-    const float4 v9 = kernel_values<kExact>(b, k0 + 2 * t + 9, tx, ty, tz);
+    float2 p01, x01, y01, z01, p89, x89, y89, z89;
+    kernel_values2<kExact>(b, k0 + 2 * t, ntx, nty, ntz, p01, x01, y01, z01);
+    kernel_values2<kExact>(b, k0 + 2 * t + 8, ntx, nty, ntz, p89, x89, y89, z89);
     unsigned ah[2][4], al[2][4];
-    split_bf16(v0.x, v1.x, ah[0][0], al[0][0]);   // tile 0 row g: phi, cols 2t, 2t+1
-    split_bf16(v0.y, v1.y, ah[0][1], al[0][1]);   // tile 0 row g+8: gx
-    split_bf16(v8.x, v9.x, ah[0][2], al[0][2]);   // cols 2t+8, 2t+9
-    split_bf16(v8.y, v9.y, ah[0][3], al[0][3]);
-    split_bf16(v0.z, v1.z, ah[1][0], al[1][0]);   // tile 1 row g: gy
-    split_bf16(v0.w, v1.w, ah[1][1], al[1][1]);   // tile 1 row g+8: gz
-    split_bf16(v8.z, v9.z, ah[1][2], al[1][2]);
-    split_bf16(v8.w, v9.w, ah[1][3], al[1][3]);
+    split_bf16x2(p01, ah[0][0], al[0][0]);   // tile 0 row g: phi, cols 2t, 2t+1
+    split_bf16x2(x01, ah[0][1], al[0][1]);   // tile 0 row g+8: gx
+    split_bf16x2(p89, ah[0][2], al[0][2]);   // cols 2t+8, 2t+9
+    split_bf16x2(x89, ah[0][3], al[0][3]);
+    split_bf16x2(y01, ah[1][0], al[1][0]);   // tile 1 row g: gy
+    split_bf16x2(z01, ah[1][1], al[1][1]);   // tile 1 row g+8: gz
+    split_bf16x2(y89, ah[1][2], al[1][2]);
+    split_bf16x2(z89, ah[1][3], al[1][3]);
     // B fragments (charges) of the 4 n8 tiles, by transposing loads: lanes 0-7 give
     // rows k0..k0+7 (n 0-7), 8-15 rows k0+8.. (n 0-7), 16-23 / 24-31 the same rows at n + 8
     const int row = k0 + (lane & 7) + ((lane >> 3) & 1) * 8;
@@ -463,6 +488,7 @@ __global__ void __launch_bounds__(kBThreads, FMM_BATCH_MIN_BLOCKS) k_p2p_batch(i
     const int lb0 = pbeg[leaf], lb1 = lb0 + pcnt[leaf];
     const int g = lane >> 2, t = lane & 3;
     const float4 tp = pos[tb + min(g, tc - 1)];   // extra rows repeat the last target
+    const float2 ntx = make_float2(-tp.x, -tp.x), nty = make_float2(-tp.y, -tp.y), ntz = make_float2(-tp.z, -tp.z);
 
     float acc[2][4][4];
 #pragma unroll
@@ -485,9 +511,18 @@ __global__ void __launch_bounds__(kBThreads, FMM_BATCH_MIN_BLOCKS) k_p2p_batch(i
         cp_async_commit();
         cp_async_wait_1();
         __syncwarp();
+        {   // move this chunk's sources into the target frame once (one source per lane)
+            float4 sp = bc.pos[lane];
+            const float4 d = bc.shift[lane];
+            sp.x += d.x;
+            sp.y += d.y;
+            sp.z += d.z;
+            bc.pos[lane] = sp;
+        }
+        __syncwarp();
         for (int k0 = 0; k0 < n_cur; k0 += 16) {
-            if (self_cur) batch_kstep<true>(bc, k0, tp.x, tp.y, tp.z, acc);
-            else batch_kstep<false>(bc, k0, tp.x, tp.y, tp.z, acc);
+            if (self_cur) batch_kstep<true>(bc, k0, ntx, nty, ntz, acc);
+            else batch_kstep<false>(bc, k0, ntx, nty, ntz, acc);
         }
         __syncwarp();
         n_cur = n_next;
