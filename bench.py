@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="all",
-                    choices=["all", "none", "adaptive", "differentiated", "batched", "systems"],
+                    choices=["all", "none", "adaptive", "differentiated", "batched", "systems", "ncrit"],
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
@@ -298,7 +298,24 @@ def run_variants(torch, stream, flush, which="all", batch_n=1048576):
         out.update(variant_batched(torch, stream, flush, batch_n))
     if which in ("all", "systems"):
         out.update(variant_systems(torch, stream, flush))
+    if which in ("all", "ncrit"):
+        out.update(variant_ncrit(torch))
     return out
+
+
+def variant_ncrit(torch):
+    """The leaf-size autotuner (fmm_tune_ncrit) on the N = 1M uniform workload,
+    P = 8, theta = 0.5: build + evaluate time for each candidate ncrit."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    N = 1048576
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    best, ms = fmm.tune_ncrit(torch.from_numpy(x).cuda(), torch.from_numpy(q.astype(np.float32)).cuda(), 8, 0.5,
+                              candidates=(24, 32, 48, 64, 96, 128), reps=3)
+    return {"ncrit_autotune_1m": {
+        "workload": "uniform cube N=1048576, P=8, theta=0.5: fmm_tune_ncrit over ncrit candidates "
+                    "(median of 3 build + evaluate each)",
+        "ms_by_ncrit": {str(k): v for k, v in ms.items()}, "best_ncrit": best,
+        "best_vs_ncrit64": ms[64] / ms[best]}}
 
 
 def variant_systems(torch, stream, flush):

@@ -263,6 +263,20 @@ int fmm_multi_info(fmm_multi *m, struct fmm_multi_info *info);
 
 int fmm_multi_destroy(fmm_multi *m);
 
+/*
+ * fmm_tune_ncrit -- the leaf size at which the evaluation is fastest for this
+ * input: the balance between M2L (more, smaller cells) and P2P (fewer, larger
+ * leaves) that the paper's auto-tuned hybrid selects by timing (Sec. 2, the
+ * M2L / P2P choice of the leaf size).  For each of the ncand candidate ncrit
+ * values (HOST array) a handle is built on x and evaluated with q (device
+ * arrays, as in fmm_evaluate) `reps` times after one warm-up; the device time of
+ * build + evaluate (median of reps) goes to ms_out[k] (HOST, ncand doubles, may
+ * be NULL) and the fastest candidate to *best (HOST).  The accuracy is set by P
+ * and theta (the MAC), not by ncrit.  Synchronous.
+ */
+int fmm_tune_ncrit(int64_t N, int P, float theta, const double *x, const float *q, const int *candidates,
+                   int ncand, int reps, const fmm_options *opt, int *best, double *ms_out);
+
 /* fmm_stats -- counters and timings of the last build/evaluate into *s (HOST). */
 int fmm_stats(fmm_handle *h, struct fmm_stats *s);
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "fmm_internal.cuh"
 
@@ -341,6 +342,60 @@ int fmm_backward(fmm_handle *w, const float *dphi, const float *dgrad, float *dq
     FMM_TRY(adjoint_p2p(h, dq, dx));
     if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
     h.backward_done = true;
+    return FMM_OK;
+}
+
+int fmm_tune_ncrit(int64_t N, int P, float theta, const double *x, const float *q, const int *candidates,
+                   int ncand, int reps, const fmm_options *opt, int *best, double *ms_out)
+{
+    if (!x || !q || !candidates || ncand < 1 || reps < 1 || !best) {
+        set_error("fmm_tune_ncrit: null argument or empty candidate list");
+        return FMM_ERR_ARG;
+    }
+    double best_ms = 1e300;
+    *best = candidates[0];
+    for (int k = 0; k < ncand; ++k) {
+        fmm_handle *w = nullptr;
+        fmm_options o = opt ? *opt : fmm_options{nullptr, -1, 0u};
+        o.flags &= ~FMM_FLAG_TIMING;
+        FMM_TRY(fmm_create(&w, N, P, theta, candidates[k], &o));
+        Handle &h = w->h;
+        int rc = FMM_OK;
+        DevBuf phi, grad;
+        std::vector<float> times;
+        {
+            DeviceGuard guard(h.device);
+            rc = phi.reserve((size_t)N * sizeof(float));
+            if (rc == FMM_OK) rc = grad.reserve((size_t)N * 3 * sizeof(float));
+            for (int r = 0; r <= reps && rc == FMM_OK; ++r) {   // r = 0: warm-up
+                if (h.events_ready) cudaEventRecord(h.ev[2 * kPhases], h.stream);
+                rc = do_build(h, x);   // synchronises; its events bracket the build
+                if (rc == FMM_OK) rc = do_evaluate(h, q, phi.as<float>(), grad.as<float>());
+                if (rc == FMM_OK && h.events_ready) {
+                    cudaEventRecord(h.ev[2 * kPhases + 1], h.stream);
+                    cudaEventSynchronize(h.ev[2 * kPhases + 1]);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, h.ev[2 * kPhases], h.ev[2 * kPhases + 1]);
+                    if (r > 0) times.push_back(ms);
+                }
+            }
+            if (rc == FMM_OK && !h.events_ready) {
+                set_error("fmm_tune_ncrit: no CUDA events");
+                rc = FMM_ERR_CUDA;
+            }
+            phi.release();
+            grad.release();
+        }
+        fmm_destroy(w);
+        if (rc != FMM_OK) return rc;
+        std::sort(times.begin(), times.end());
+        const double med = times[times.size() / 2];
+        if (ms_out) ms_out[k] = med;
+        if (med < best_ms) {
+            best_ms = med;
+            *best = candidates[k];
+        }
+    }
     return FMM_OK;
 }
 

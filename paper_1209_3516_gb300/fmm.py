@@ -97,6 +97,9 @@ def load():
     L.fmm_multi_evaluate.argtypes = [_vp, _vp, _vp, _vp]
     L.fmm_multi_info.argtypes = [_vp, ctypes.POINTER(_MultiInfo)]
     L.fmm_multi_destroy.argtypes = [_vp]
+    L.fmm_tune_ncrit.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, _vp, _vp, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
 
@@ -119,6 +122,23 @@ def _dev_ptr(t, dtype, shape, name):
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError("%s must be contiguous with shape %s, got %s" % (name, shape, tuple(t.shape)))
     return t.data_ptr()
+
+
+def tune_ncrit(x, q, P, theta, candidates=(16, 32, 48, 64, 96, 128), reps=3, stream=None):
+    """fmm_tune_ncrit: (best ncrit, {ncrit: median ms of build + evaluate})."""
+    import torch
+    N = x.shape[0]
+    xp = _dev_ptr(x, torch.float64, (N, 3), "x")
+    qp = _dev_ptr(q, torch.float32, (N,), "q")
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    opt = _Options(ctypes.c_void_p(stream.cuda_stream), x.device.index or 0, 0)
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    ms = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_int()
+    _check(load().fmm_tune_ncrit(N, int(P), float(theta), xp, qp, cand, len(candidates), int(reps),
+                                 ctypes.byref(opt), ctypes.byref(best), ms))
+    return best.value, {c: ms[i] for i, c in enumerate(candidates)}
 
 
 def energy_noalloc(q, phi, E, stream=None):

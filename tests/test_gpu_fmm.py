@@ -252,6 +252,21 @@ def test_full_size_uniform_1m(torch_cuda, P, theta):
     h.close()
 
 
+def test_tune_ncrit(torch_cuda):
+    # the leaf-size autotuner returns the fastest candidate of its own timings
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 30000
+    x, q = inputs.uniform_cube(N, 1500)
+    best, ms = fmm.tune_ncrit(torch.from_numpy(x).cuda(), torch.from_numpy(q.astype(np.float32)).cuda(), 4, 0.4,
+                              candidates=(16, 32, 64, 128), reps=2)
+    assert best in ms and all(v > 0 for v in ms.values())
+    assert ms[best] == min(ms.values())
+    with pytest.raises(fmm.FMMError):
+        fmm.tune_ncrit(torch.from_numpy(x).cuda(), torch.from_numpy(q.astype(np.float32)).cuda(), 4, 0.4,
+                       candidates=(0,), reps=1)
+
+
 KAHAN_CASES = [
     # N, P, theta, ncrit, kind ("p": Plummer with the equal charges 1/N of the adaptive workload)
     (20000, 4, 0.4, 32, "p"),
