@@ -9,8 +9,8 @@
 //
 // Kernel layout:
 //   P2M  one warp per leaf, lanes over its particles, warp reduction;
-//   M2M  one thread per cell of a level (P <= 6) or one warp per cell with
-//        three one-dimensional shifts (P = 8), summing its children (bottom-up);
+//   M2M  one warp per cell of a level: three one-dimensional shifts of all its
+//        children at once, then their sum (bottom-up);
 //   M2L  one warp per target cell, lanes over its M2L sources, each lane
 //        computing the kernel derivatives D_m(R) of its pair and contracting,
 //        then a warp reduction of the T local coefficients;
@@ -143,54 +143,6 @@ __global__ void k_p2m(int nleaves, const int *leaf_list, const int *pbeg, const 
 // M2M: Mb_k(P) = sum_{m <= k} Mb_m(C) 2^-|m| w_{k-m}((X_P - X_C) / s_P)
 // (child half-width s_C = s_P / 2, (X_P - X_C) / s_P = -(+-1/2) per axis)
 // ---------------------------------------------------------------------------
-// P <= 6: one thread per cell of a level, fully unrolled.
-template <int P>
-__global__ void k_m2m(int lo, int n, const int *cbeg, const int *ccnt, const float4 *geom, float *M)
-{
-    constexpr int T = MI<P>::T, TP = MI<P>::TP;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = lo + i;
-    const int nch = ccnt[c];
-    if (nch == 0) return;   // leaf: its multipole comes from P2M
-    const float4 Xp = geom[c];
-    float acc[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = 0.0f;
-    for (int k = 0; k < nch; ++k) {
-        const int ch = cbeg[c] + k;
-        const float4 Xc = geom[ch];
-        float w[T];
-        taylor_monomials<P>(Xc.x > Xp.x ? -0.5f : 0.5f, Xc.y > Xp.y ? -0.5f : 0.5f, Xc.z > Xp.z ? -0.5f : 0.5f, w);
-        float mc[T];
-        const float *src = M + (size_t)ch * TP;
-#pragma unroll
-        for (int t = 0; t < T; ++t) mc[t] = src[t];
-#pragma unroll
-        for (int nk = 0; nk < P; ++nk)
-#pragma unroll
-            for (int ka = nk; ka >= 0; --ka)
-#pragma unroll
-                for (int kb = nk - ka; kb >= 0; --kb) {
-                    const int kc = nk - ka - kb;
-                    float s = 0.0f;
-#pragma unroll
-                    for (int ma = 0; ma <= ka; ++ma)
-#pragma unroll
-                        for (int mb = 0; mb <= kb; ++mb)
-#pragma unroll
-                            for (int mc_ = 0; mc_ <= kc; ++mc_) {
-                                const float scale = 1.0f / (float)(1 << (ma + mb + mc_));
-                                s = fmaf(mc[MI<P>::idx(ma, mb, mc_)] * scale, w[MI<P>::idx(ka - ma, kb - mb, kc - mc_)], s);
-                            }
-                    acc[MI<P>::idx(ka, kb, kc)] += s;
-                }
-    }
-    float *dst = M + (size_t)c * TP;
-#pragma unroll
-    for (int t = 0; t < TP; ++t) dst[t] = t < T ? acc[t] : 0.0f;
-}
-
 // Storage index of (a, b, c) and its inverse (degree-graded order of mi.cuh).
 __device__ __forceinline__ int mi_index(int a, int b, int c)
 {
@@ -215,94 +167,85 @@ __device__ __forceinline__ void mi_decode(int i, int &a, int &b, int &c)
 // i.e. three one-dimensional shifts (along x, then y, then z), each
 //   A_k = sum_{j = 0..k_i} B_{k - j e_i} (-s_i)^j / j!,
 // which read only lower indices of the same truncated set.  One warp per
-// parent cell, lanes over the output coefficients, the intermediate arrays
-// in shared memory.
+// parent cell; all of its children are shifted at once: the work items of a
+// pass are the (child, coefficient) pairs, spread over the lanes, with the
+// children's coefficients, the decoded multi-indices and the per-axis factors
+// in shared memory (no division, no dependence between children).
+constexpr int kM2MWarps = 4;
+
 template <int P>
-__global__ void __launch_bounds__(128) k_m2m_sep(int lo, int n, const int *cbeg, const int *ccnt,
-                                                 const float4 *geom, float *M)
+__global__ void __launch_bounds__(kM2MWarps * 32) k_m2m_sep(int lo, int n, const int *cbeg, const int *ccnt,
+                                                              const float4 *geom, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
-    constexpr int KPL = (T + 31) / 32;   // outputs per lane
-    __shared__ float buf_s[4][2][TP];
+    __shared__ float buf_s[kM2MWarps][2][8][T];
+    __shared__ float fac_s[kM2MWarps][8][3][P];   // (-s_i)^j / j! per child and axis
+    __shared__ unsigned char abc_s[T][4];          // multi-index (a, b, c, |k|) of each storage index
     const int w = threadIdx.x >> 5;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = (int)lane_id();
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        int a, b, c;
+        mi_decode(k, a, b, c);
+        abc_s[k][0] = (unsigned char)a;
+        abc_s[k][1] = (unsigned char)b;
+        abc_s[k][2] = (unsigned char)c;
+        abc_s[k][3] = (unsigned char)(a + b + c);
+    }
+    __syncthreads();
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const int c = lo + i;
     const int nch = ccnt[c];
     if (nch == 0) return;   // leaf: its multipole comes from P2M
-    float *b0 = buf_s[w][0], *b1 = buf_s[w][1];
-    int ka[KPL], kb[KPL], kc[KPL];
-    float acc[KPL];
-#pragma unroll
-    for (int j = 0; j < KPL; ++j) {
-        acc[j] = 0.0f;
-        const int k = lane + 32 * j;
-        if (k < T) mi_decode(k, ka[j], kb[j], kc[j]);
-        else ka[j] = kb[j] = kc[j] = 0;
-    }
+    const int cb = cbeg[c];
     const float4 Xp = geom[c];
-    for (int q = 0; q < nch; ++q) {
-        const int ch = cbeg[c] + q;
-        const float4 Xc = geom[ch];
-        // factor per axis: (-s_i)^j / j!, -s_i = -1 when the child lies above the parent centre
-        const float sx = Xc.x > Xp.x ? -1.0f : 1.0f, sy = Xc.y > Xp.y ? -1.0f : 1.0f,
-                    sz = Xc.z > Xp.z ? -1.0f : 1.0f;
-        const float *mc = M + (size_t)ch * TP;
-        for (int k = lane; k < T; k += 32) b0[k] = mc[k];
-        __syncwarp();
-        float t[KPL];
-        // x shift: b0 -> b1
-#pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-            t[j] = 0.0f;
-            if (lane + 32 * j >= T) continue;
-            float f = 1.0f;
-            for (int d = 0; d <= ka[j]; ++d) {
-                t[j] = fmaf(b0[mi_index(ka[j] - d, kb[j], kc[j])], f, t[j]);
-                f *= sx / (float)(d + 1);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < KPL; ++j)
-            if (lane + 32 * j < T) b1[lane + 32 * j] = t[j];
-        __syncwarp();
-        // y shift: b1 -> b0 (b0 is no longer read by anyone)
-#pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-            t[j] = 0.0f;
-            if (lane + 32 * j >= T) continue;
-            float f = 1.0f;
-            for (int d = 0; d <= kb[j]; ++d) {
-                t[j] = fmaf(b1[mi_index(ka[j], kb[j] - d, kc[j])], f, t[j]);
-                f *= sy / (float)(d + 1);
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < KPL; ++j)
-            if (lane + 32 * j < T) b0[lane + 32 * j] = t[j];
-        __syncwarp();
-        // z shift, accumulated over the children
-#pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-            if (lane + 32 * j >= T) continue;
-            float s = 0.0f, f = 1.0f;
-            for (int d = 0; d <= kc[j]; ++d) {
-                s = fmaf(b0[mi_index(ka[j], kb[j], kc[j] - d)], f, s);
-                f *= sz / (float)(d + 1);
-            }
-            acc[j] += s;
-        }
-        __syncwarp();   // b0 is refilled by the next child
+    float(*A)[T] = buf_s[w][0];
+    float(*B)[T] = buf_s[w][1];
+    for (int e = lane; e < nch * 3 * P; e += 32) {
+        const int ch = e / (3 * P), ax = (e / P) % 3, j = e % P;
+        const float4 Xc = geom[cb + ch];
+        const float pc = ax == 0 ? Xc.x : (ax == 1 ? Xc.y : Xc.z), pp = ax == 0 ? Xp.x : (ax == 1 ? Xp.y : Xp.z);
+        float f = 1.0f;
+        const float sgn = pc > pp ? -1.0f : 1.0f;
+        for (int d = 1; d <= j; ++d) f *= sgn * (1.0f / (float)d);   // constant per call: d <= 7
+        fac_s[w][ch][ax][j] = f;
     }
-    float *dst = M + (size_t)c * TP;
-#pragma unroll
-    for (int j = 0; j < KPL; ++j) {
-        const int k = lane + 32 * j;
-        if (k < T) dst[k] = ldexpf(acc[j], -(ka[j] + kb[j] + kc[j]));
+    for (int e = lane; e < nch * T; e += 32) {
+        const int ch = e / T, k = e % T;
+        A[ch][k] = M[(size_t)(cb + ch) * TP + k];
     }
-    for (int k = T + lane; k < TP; k += 32) dst[k] = 0.0f;
+    __syncwarp();
+    // three passes: x (A -> B), y (B -> A), z (A -> B)
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        float(*src)[T] = (ax == 1) ? B : A;
+        float(*dst)[T] = (ax == 1) ? A : B;
+        for (int e = lane; e < nch * T; e += 32) {
+            const int ch = e / T, k = e % T;
+            const int ka = abc_s[k][0], kb = abc_s[k][1], kc = abc_s[k][2];
+            const int kx = ax == 0 ? ka : (ax == 1 ? kb : kc);
+            const float *f = fac_s[w][ch][ax];
+            float t = 0.0f;
+#pragma unroll
+            for (int d = 0; d < P; ++d) {
+                if (d > kx) break;
+                const int ia = ax == 0 ? ka - d : ka, ib = ax == 1 ? kb - d : kb, ic = ax == 2 ? kc - d : kc;
+                t = fmaf(src[ch][mi_index(ia, ib, ic)], f[d], t);
+            }
+            dst[ch][k] = t;
+        }
+        __syncwarp();
+    }
+    // sum over the children, scale by 2^-|k|
+    float *out = M + (size_t)c * TP;
+    for (int k = lane; k < TP; k += 32) {
+        float s = 0.0f;
+        if (k < T) {
+            for (int ch = 0; ch < nch; ++ch) s += B[ch][k];
+            s *= 1.0f / (float)(1 << abc_s[k][3]);
+        }
+        out[k] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -424,12 +367,8 @@ template <int P> static int m2m_levels(Handle &h, float *M)
     for (int l = h.nlevels - 2; l >= 0; --l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
         ++h.launches;
-        if (P >= 8)
-            k_m2m_sep<P><<<ceil_div((int64_t)n * 32, 128), 128, 0, h.stream>>>(
-                lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), M);
-        else
-            k_m2m<P><<<ceil_div(n, 64), 64, 0, h.stream>>>(lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
-                                                           h.c_geom.as<float4>(), M);
+        k_m2m_sep<P><<<ceil_div((int64_t)n * 32, kM2MWarps * 32), kM2MWarps * 32, 0, h.stream>>>(
+            lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), M);
     }
     FMM_CHECK_LAUNCH("upward pass");
     return FMM_OK;
