@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
     RunCursor cur;
     cur.init(roff, it.w, run, run_end);
     if (tc <= 4) adj_stream<4>(cur, run, run_end, pos, adj, buf, lb0, lb1, t, a2);
+    else if (tc <= 6) adj_stream<6>(cur, run, run_end, pos, adj, buf, lb0, lb1, t, a2);
     else adj_stream<kAdjG>(cur, run, run_end, pos, adj, buf, lb0, lb1, t, a2);
     // acc[4 g + k]: component k of target g
     float acc[4 * kAdjG];

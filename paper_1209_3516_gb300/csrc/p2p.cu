@@ -294,13 +294,20 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     RunCursor cur;
     cur.init(roff, it.w, run, run_end);
     // the item computes ceil(tc / 4) * 4 targets (extra ones repeat the last target)
-    const int nt4 = (tc + 3) >> 2;
-    if (nt4 == 1) {
+    // the item computes tc rounded up to 4 (tc <= 8) or to 2 (tc > 8) targets, extra
+    // ones repeating the last target: balanced slices of leaves of 13-55
+    // particles hold 9-16 targets, where rounding to 4 would add ~9 % of pairs
+    const int ntr = tc <= 4 ? 4 : tc <= 8 ? 8 : (tc + 1) & ~1;
+    if (ntr == 4) {
         p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
-    } else if (G > 8 && nt4 == 2) {
-        p2p_stream<8, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
-    } else if (G > 12 && nt4 == 3) {
-        p2p_stream<(G > 12 ? 12 : G), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (G <= 8 || ntr == 8) {
+        p2p_stream<(G < 8 ? G : 8), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (ntr == 10) {
+        p2p_stream<(G < 10 ? G : 10), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (ntr == 12) {
+        p2p_stream<(G < 12 ? G : 12), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    } else if (ntr == 14) {
+        p2p_stream<(G < 14 ? G : 14), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else {
         p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     }
