@@ -332,3 +332,79 @@ def test_full_size_plummer_4m_kahan(torch_cuda):
           "P2P %d pairs %d" % (rel_l2(phi[t], pd), rel_l2(grad[t], gd), E, st["ncells"], st["nlevels"],
                                st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
     h.close()
+
+
+def _edge_inputs(kind, N, seed):
+    g = inputs.rng(seed)
+    if kind == "plane":          # every point at z = 0.3: zero extent along one axis
+        x = np.concatenate([g.random((N, 2)), np.full((N, 1), 0.3)], axis=1)
+    elif kind == "far":          # a unit cube far from the origin: the FP64 normalisation must absorb it
+        x = g.random((N, 3)) + np.array([1.0e6, -2.5e5, 3.0e4])
+    elif kind == "clusters":     # two tight clusters far apart: deep, unbalanced tree
+        x = np.concatenate([0.01 * g.standard_normal((N // 2, 3)),
+                            10.0 + 0.01 * g.standard_normal((N - N // 2, 3))])
+    elif kind == "line":         # points on a segment: two degenerate axes
+        t = g.random((N, 1))
+        x = np.concatenate([t, 2 * t, -t], axis=1)
+    else:                        # a 16^3 lattice: many particles on cell boundaries and centres
+        k = np.arange(16) / 16.0
+        x = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)[:N]
+    q = g.random(N) * 2 - 1
+    return x, q
+
+
+def fp32_position_floor(ref, q, phi_ref, grad_ref):
+    """Relative L2 error that FP32 positions alone can cause.  The library stores
+    each particle as an FP32 offset from the centre of its leaf's parent (half-
+    width s_p in normalised units), so each component is off by at most
+    2^-24 s_p and the particle by |du_i| <= sqrt(3) 2^-24 s_p.  A pair term
+    q_j / r then moves by at most |q_j| (|du_i| + |du_j|) / r^2, and the
+    gradient term by 3 |q_j| (|du_i| + |du_j|) / r^3; summed over all pairs
+    (an over-estimate: the far ones go through expansions) this bounds the
+    error of phi and grad of an otherwise exact evaluation."""
+    c = ref.cells()
+    rs = ref.sorted()
+    u = rs["u"]                                  # normalised positions, sorted order
+    du = np.zeros(len(u))
+    leaves = np.nonzero(c["nchild"] == 0)[0]
+    for lf in leaves:
+        par = c["parent"][lf]
+        lev = c["level"][par] if par >= 0 else c["level"][lf]
+        b, n = c["pbeg"][lf], c["pcnt"][lf]
+        du[b:b + n] = np.sqrt(3.0) * 2.0 ** -24 * 2.0 ** -float(lev)
+    qs = np.asarray(q)[rs["perm"]]
+    d = u[:, None, :] - u[None, :, :]
+    r = np.sqrt((d * d).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    r[r == 0] = np.inf
+    e = du[:, None] + du[None, :]
+    dphi = (np.abs(qs)[None, :] * e / r ** 2).sum(1)
+    dgrad = 3.0 * (np.abs(qs)[None, :] * e / r ** 3).sum(1)
+    _, h = ref.norm()
+    inv = np.empty_like(rs["perm"])
+    inv[rs["perm"]] = np.arange(len(inv))
+    # back to caller order and physical units (phi / h, grad / h^2)
+    bphi = np.linalg.norm(dphi[inv] / h) / np.linalg.norm(phi_ref)
+    bgrad = np.linalg.norm(dgrad[inv] / h ** 2) / np.linalg.norm(grad_ref)
+    return bphi, bgrad
+
+
+@pytest.mark.parametrize("kind,N", [("plane", 8000), ("far", 8000), ("clusters", 12000), ("line", 3000),
+                                    ("lattice", 4096)])
+def test_parity_on_degenerate_geometries(torch_cuda, kind, N):
+    # flat, shifted, clustered, one-dimensional and lattice inputs: the tree and
+    # lists stay bit-exact; potential and gradient stay within 1e-5 or, where
+    # the input has pairs far closer than its leaves are wide (random points on
+    # a plane or a line), within twice the FP32-position floor computed above
+    x, q = _edge_inputs(kind, N, 1600 + N)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, 4, 0.4, 32)
+    ref = oracle.FMM(N, 4, 0.4, 32).build(x)
+    check_structure(h, ref)
+    pr, gr = ref.evaluate(q32)
+    bphi, bgrad = fp32_position_floor(ref, q32, pr, gr)
+    ephi, egrad = rel_l2(phi, pr), rel_l2(grad, gr)
+    print("%s: rel err phi %.2e grad %.2e; FP32-position floor phi %.2e grad %.2e" % (kind, ephi, egrad, bphi, bgrad))
+    assert ephi <= max(TOL, 2 * bphi), (ephi, bphi)
+    assert egrad <= max(TOL, 2 * bgrad), (egrad, bgrad)
+    h.close()
