@@ -408,3 +408,41 @@ def test_parity_on_degenerate_geometries(torch_cuda, kind, N):
     assert ephi <= max(TOL, 2 * bphi), (ephi, bphi)
     assert egrad <= max(TOL, 2 * bgrad), (egrad, bgrad)
     h.close()
+
+
+@pytest.mark.slow
+def test_config_sweep_1m(torch_cuda):
+    # the plain workload's sweep: N = 1,048,576 uniform, P in {3,4,6,8} x theta in
+    # {0.3,0.4,0.5}, ncrit = 64; error against the FP64 direct sum on the 4,096-target
+    # sample for every configuration, with the device time of build + evaluate
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 1048576
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    q32 = q.astype(np.float32)
+    t = inputs.sample_targets(N, 4096)
+    pd, gd = oracle.direct(x, q32.astype(np.float64), t)
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q32).cuda()
+    err = {}
+    print("\nP theta | err phi  err grad | build ms  eval ms | evals/s | P2P pairs")
+    for P in (3, 4, 6, 8):
+        for theta in (0.3, 0.4, 0.5):
+            h = fmm.FMM(N, P, theta, 64, timing=True)
+            for _ in range(3):
+                h.build(xd)
+                phi, grad = h.evaluate(qd)
+            torch.cuda.synchronize()
+            st = h.stats()
+            e = (rel_l2(phi.cpu().numpy()[t], pd), rel_l2(grad.cpu().numpy()[t], gd))
+            err[(P, theta)] = e
+            print("%d %.1f | %.2e %.2e | %.3f %.3f | %.1f | %d" % (P, theta, e[0], e[1], st["ms_build"],
+                                                                 st["ms_evaluate"],
+                                                                 1e3 / (st["ms_build"] + st["ms_evaluate"]),
+                                                                 st["p2p_pairs"]))
+            h.close()
+    # the error falls with P at every theta and rises with theta at every P
+    for theta in (0.3, 0.4, 0.5):
+        assert err[(3, theta)][0] > err[(4, theta)][0] > err[(6, theta)][0] > err[(8, theta)][0]
+    for P in (3, 4, 6, 8):
+        assert err[(P, 0.3)][1] < err[(P, 0.4)][1] < err[(P, 0.5)][1]
+    assert max(err[(8, 0.5)]) <= 1e-4   # the benchmark configuration meets the metric's accuracy
