@@ -446,3 +446,42 @@ def test_config_sweep_1m(torch_cuda):
     for P in (3, 4, 6, 8):
         assert err[(P, 0.3)][1] < err[(P, 0.4)][1] < err[(P, 0.5)][1]
     assert max(err[(8, 0.5)]) <= 1e-4   # the benchmark configuration meets the metric's accuracy
+
+
+@pytest.mark.slow
+def test_plummer_4m_sweep(torch_cuda):
+    # the adaptive workload's sweep: N = 4,194,304 Plummer, charges 1/N, theta = 0.4,
+    # P in {4, 8} x ncrit in {32, 64, 128}, compensated P2P: error against the FP64
+    # direct sum on the 4,096-target sample; P = 8, ncrit = 128 also against the
+    # oracle FMM (the P = 4, ncrit = 64 point is test_full_size_plummer_4m_kahan)
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N, theta = 4194304, 0.4
+    x, q = inputs.plummer(N, inputs.SEED_BASE + 2)
+    q32 = q.astype(np.float32)
+    t = inputs.sample_targets(N, 4096)
+    pd, gd = oracle.direct(x, q32.astype(np.float64), t)
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q32).cuda()
+    err = {}
+    print("\nP ncrit | err phi  err grad | build ms  eval ms | levels cells | P2P pairs")
+    for P in (4, 8):
+        for ncrit in (32, 64, 128):
+            h = fmm.FMM(N, P, theta, ncrit, kahan=True, timing=True)
+            for _ in range(2):
+                h.build(xd)
+                phi, grad = h.evaluate(qd)
+            torch.cuda.synchronize()
+            st = h.stats()
+            phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+            e = (rel_l2(phi[t], pd), rel_l2(grad[t], gd))
+            err[(P, ncrit)] = e
+            print("%d %d | %.2e %.2e | %.2f %.2f | %d %d | %d" % (P, ncrit, e[0], e[1], st["ms_build"],
+                                                                st["ms_evaluate"], st["nlevels"], st["ncells"],
+                                                                st["p2p_pairs"]))
+            if (P, ncrit) == (8, 128):
+                pr, gr = oracle.FMM(N, P, theta, ncrit).build(x).evaluate(q32.astype(np.float64), t)
+                assert rel_l2(phi[t], pr) <= TOL and rel_l2(grad[t], gr) <= TOL
+            h.close()
+    for ncrit in (32, 64, 128):
+        assert err[(8, ncrit)][1] < err[(4, ncrit)][1]   # the higher order is the more accurate
+        assert err[(8, ncrit)][0] <= 1e-4 and err[(8, ncrit)][1] <= 1e-4
