@@ -93,6 +93,21 @@ struct DeviceGuard {
     }
 };
 
+// Errors that kernels record asynchronously (bit 1 of err_flag: a bounded wait of
+// the P2P staging gave up); read at the synchronising entry points.
+static int check_async_errors(Handle &h)
+{
+    if (!h.err_flag.p) return FMM_OK;
+    FMM_CUDA(cudaMemcpyAsync(&h.pinned->err, h.err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    if (h.pinned->err & 2u) {
+        FMM_CUDA(cudaMemsetAsync(h.err_flag.p, 0, sizeof(unsigned), h.stream));
+        set_error("P2P staging: a bulk-copy wait gave up; the last evaluation is incomplete");
+        return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
 static int do_build(Handle &h, const double *x)
 {
     h.built = false;
@@ -297,7 +312,7 @@ int fmm_evaluate_host(fmm_handle *w, const double *x_host, const float *q_host, 
     FMM_CUDA(cudaStreamSynchronize(h.stream));
     // the device copy of x is internal: a later fmm_evaluate(x = caller pointer) must rebuild
     h.x_built = nullptr;
-    return FMM_OK;
+    return check_async_errors(h);
 }
 
 int fmm_energy(fmm_handle *w, double *E)
@@ -312,6 +327,7 @@ int fmm_energy(fmm_handle *w, double *E)
         return FMM_ERR_STATE;
     }
     DeviceGuard guard(h.device);
+    FMM_TRY(check_async_errors(h));
     return energy_reduce(h, E);
 }
 
@@ -407,6 +423,7 @@ int fmm_stats(fmm_handle *w, struct fmm_stats *s)
     }
     Handle &h = w->h;
     DeviceGuard guard(h.device);
+    FMM_TRY(check_async_errors(h));
     std::memset(s, 0, sizeof(*s));
     s->n = h.N;
     s->ncells = h.ncells;

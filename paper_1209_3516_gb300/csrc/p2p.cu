@@ -55,7 +55,16 @@ constexpr int kP2PThreads = 128;
 #endif
 constexpr int kSlots = FMM_P2P_SLOTS;   // staged source particles per buffer
 constexpr int kP2PUnroll = FMM_P2P_UNROLL;   // staged sources per lane per loop iteration
-constexpr int kP2PSmem = (kP2PThreads / 32) * 4 * kSlots * (int)sizeof(float4);   // 2 buffers x (particles + shifts)
+// Staging by bulk copies (cp.async.bulk, the TMA engine, completion on an
+// mbarrier with bounded waits) instead of per-lane 16-byte cp.async: correct,
+// but 3.5 % slower on this ALU-bound kernel (7.34 vs 7.08 ms at N = 1M, P = 8):
+// one lane issues the copies and every lane polls the mbarrier.  Off by default.
+#ifndef FMM_P2P_BULK
+#define FMM_P2P_BULK 0
+#endif
+constexpr bool kP2PBulk = FMM_P2P_BULK != 0;
+// 2 buffers x (particles + shifts) per warp, then two mbarriers per warp
+constexpr int kP2PSmem = (kP2PThreads / 32) * (4 * kSlots * (int)sizeof(float4) + 2 * 8);
 
 
 // Work items: one per slice of <= 16 targets of a leaf, slices balanced in size;
@@ -200,23 +209,44 @@ __device__ __forceinline__ void p2p_tile(const float4 &s, const float2 *ntx, con
 // copied while the current one is used) and NT targets per staged source.
 // With kKahan the per-chunk partial sums (blk) are added to v with Kahan
 // compensation (comp) once per chunk.
+// Returns false if a bulk-copy wait gave up (the item's results are then not
+// written; the caller flags the error).
 template <int NT, bool kKahan>
-__device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
-                                           float4 *buf, int lb0, int lb1, const float2 *ntx, const float2 *nty,
-                                           const float2 *ntz, float2 *v, float2 *comp, float2 *blk)
+__device__ __forceinline__ bool p2p_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
+                                           float4 *buf, unsigned long long *mbar, int lb0, int lb1,
+                                           const float2 *ntx, const float2 *nty, const float2 *ntz, float2 *v,
+                                           float2 *comp, float2 *blk)
 {
     const int lane = (int)lane_id();
     bool self_cur = false, self_next = false;
-    int n_cur = cur.stage<kSlots, false>(run, run_end, pos, nullptr, buf, nullptr, buf + kSlots, lb0, lb1, &self_cur);
-    cp_async_commit();
+    int n_cur;
+    if (kP2PBulk) {
+        n_cur = cur.stage_bulk<kSlots>(run, run_end, pos, buf, buf + kSlots, lb0, lb1, &self_cur, mbar);
+    } else {
+        n_cur = cur.stage<kSlots, false>(run, run_end, pos, nullptr, buf, nullptr, buf + kSlots, lb0, lb1,
+                                         &self_cur);
+        cp_async_commit();
+    }
     for (int c = 0; n_cur > 0; ++c) {
         float4 *cur_part = buf + (c & 1) * (2 * kSlots);
         float4 *cur_shift = cur_part + kSlots;
         float4 *nx = buf + ((c + 1) & 1) * (2 * kSlots);
-        const int n_next =
-            cur.stage<kSlots, false>(run, run_end, pos, nullptr, nx, nullptr, nx + kSlots, lb0, lb1, &self_next);
-        cp_async_commit();
-        cp_async_wait_1();
+        int n_next;
+        if (kP2PBulk) {
+            // buffer b's j-th fill completes phase j of mbar[b]: chunk c is fill c / 2 of buffer c & 1
+            n_next = cur.stage_bulk<kSlots>(run, run_end, pos, nx, nx + kSlots, lb0, lb1, &self_next,
+                                            mbar + ((c + 1) & 1));
+            if (!mbar_wait_warp(mbar + (c & 1), (unsigned)(c >> 1) & 1u)) {
+                // give up on this item, but let the copies already issued land first
+                mbar_wait_warp(mbar + ((c + 1) & 1), (unsigned)((c + 1) >> 1) & 1u);
+                return false;
+            }
+        } else {
+            n_next = cur.stage<kSlots, false>(run, run_end, pos, nullptr, nx, nullptr, nx + kSlots, lb0, lb1,
+                                              &self_next);
+            cp_async_commit();
+            cp_async_wait_1();
+        }
         __syncwarp();
         float2 *acc = kKahan ? blk : v;
 #pragma unroll kP2PUnroll
@@ -247,6 +277,7 @@ __device__ __forceinline__ void p2p_stream(RunCursor &cur, const float4 *run, co
         n_cur = n_next;
         self_cur = self_next;
     }
+    return true;
 }
 
 template <int P, bool kKahan, int G>
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
                                                      const int *parent, const float4 *geom, const float *L,
                                                      const int *perm, float phi_scale, float grad_scale,
                                                      const float2 *cell_scale, float *phi, float *grad,
-                                                     float *phi_sorted)
+                                                     float *phi_sorted, unsigned *err)
 {
     static_assert(G % 4 == 0 && G <= 16, "targets per item");
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
@@ -265,6 +296,16 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     if (item >= nitems) return;
     const unsigned lane = lane_id();
     float4 *buf = p2p_smem + (threadIdx.x >> 5) * (4 * kSlots);   // [2][particles, shifts][kSlots]
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(p2p_smem + (kP2PThreads / 32) * (4 * kSlots)) +
+                               2 * (threadIdx.x >> 5);
+    if (kP2PBulk) {
+        if (lane == 0) {
+            mbar_init(mbar, 1);
+            mbar_init(mbar + 1, 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
     const int4 it = items[item];
     const int leaf = it.x, tb = it.y, tc = it.z;
     const int lb0 = pbeg[leaf], lb1 = lb0 + pcnt[leaf];   // the target leaf's own particles
@@ -298,18 +339,23 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     // ones repeating the last target: balanced slices of leaves of 13-55
     // particles hold 9-16 targets, where rounding to 4 would add ~9 % of pairs
     const int ntr = tc <= 4 ? 4 : tc <= 8 ? 8 : (tc + 1) & ~1;
+    bool staged = true;
     if (ntr == 4) {
-        p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<4, kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else if (G <= 8 || ntr == 8) {
-        p2p_stream<(G < 8 ? G : 8), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<(G < 8 ? G : 8), kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else if (ntr == 10) {
-        p2p_stream<(G < 10 ? G : 10), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<(G < 10 ? G : 10), kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else if (ntr == 12) {
-        p2p_stream<(G < 12 ? G : 12), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<(G < 12 ? G : 12), kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else if (ntr == 14) {
-        p2p_stream<(G < 14 ? G : 14), kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<(G < 14 ? G : 14), kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
     } else {
-        p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+        staged = p2p_stream<G, kKahan>(cur, run, run_end, pos, buf, mbar, lb0, lb1, ntx, nty, ntz, a, comp, blk);
+    }
+    if (!staged) {   // a bulk-copy wait gave up: flag it, write nothing for this item
+        if (lane == 0) atomicOr(err, 2u);
+        return;
     }
     if (kKahan) {   // fold the outstanding compensation into the sums
 #pragma unroll
@@ -448,7 +494,7 @@ template <int P, bool kKahan, int G> static int p2p_launch(Handle &h, float *phi
         (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
         h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
         h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale,
-        h.c_scale.as<float2>(), phi, grad, h.phi_sorted.as<float>());
+        h.c_scale.as<float2>(), phi, grad, h.phi_sorted.as<float>(), h.err_flag.as<unsigned>());
     FMM_CHECK_LAUNCH("p2p");
     return FMM_OK;
 }

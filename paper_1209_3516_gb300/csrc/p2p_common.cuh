@@ -24,6 +24,54 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Bulk-copy (TMA) staging: one lane issues one cp.async.bulk per contiguous
+// run segment (16-byte aligned, a multiple of 16 bytes: float4 particles), the
+// bytes counted on a per-buffer mbarrier that the consumers wait on.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *mbar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mbar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(mbar)), "r"(parity)
+                 : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+// Every lane waits for the phase of the given parity (a bounded number of
+// polls); false for the whole warp if any lane gave up.
+constexpr unsigned kMbarPolls = 1u << 20;
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long *mbar, unsigned parity)
+{
+    bool done = false;
+    for (unsigned i = 0; i < kMbarPolls && !done; ++i) done = mbar_try_wait(mbar, parity);
+    return __all_sync(kFull, done);
+}
+
 // Warp-uniform cursor over an item's source runs, filling staging buffers.
 struct RunCursor {
     int e, e1, o, pb, cnt;
@@ -75,6 +123,39 @@ struct RunCursor {
                 load(run, run_end);
             }
         }
+        *self = sf;
+        return slots;
+    }
+    // The same walk with bulk copies: lane 0 issues one copy per run segment into
+    // part and, last, the arrive on mbar (the buffer's previous contents have
+    // been read by every lane: the caller has passed a __syncwarp).
+    template <int kS>
+    __device__ __forceinline__ int stage_bulk(const float4 *run, const int *run_end, const float4 *pos, float4 *part,
+                                              float4 *shift, int tb0, int tb1, bool *self, unsigned long long *mbar)
+    {
+        const int lane = (int)lane_id();
+        int slots = 0;
+        bool sf = false;
+        if (lane == 0) fence_proxy_async();
+        while (slots < kS && e < e1) {
+            const int m = min(cnt - o, kS - slots);
+            const int begin = pb + o;
+            sf |= begin < tb1 && begin + m > tb0;
+            if (lane == 0) {
+                mbar_expect_tx(mbar, (unsigned)m * 16u);
+                bulk_g2s(part + slots, pos + begin, (unsigned)m * 16u, mbar);
+            }
+            const float4 sh = make_float4(shx, shy, shz, 0.0f);
+            for (int i = lane; i < m; i += 32) shift[slots + i] = sh;
+            slots += m;
+            o += m;
+            if (o == cnt) {
+                ++e;
+                o = 0;
+                load(run, run_end);
+            }
+        }
+        if (lane == 0) mbar_arrive(mbar);
         *self = sf;
         return slots;
     }
