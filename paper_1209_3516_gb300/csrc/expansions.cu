@@ -13,7 +13,8 @@
 //        children at once, then their sum (bottom-up);
 //   M2L  one warp per target cell, lanes over its M2L sources, each lane
 //        computing the kernel derivatives D_m(R) of its pair and contracting,
-//        then a warp reduction of the T local coefficients;
+//        then a warp reduction of the T local coefficients (at P = 8 in two
+//        launches, each owning half of the output coefficients);
 //   L2L  one thread per cell of a level, from its parent (top-down).
 #include <cuda_runtime.h>
 
@@ -253,10 +254,12 @@ __global__ void __launch_bounds__(kM2MWarps * 32) k_m2m_sep(int lo, int n, const
 // One warp per target cell, lanes over its M2L sources; each lane computes the
 // kernel derivatives of its pair and contracts them with the source multipole
 // (streamed from memory as float4) into the output coefficients
-// N0 <= idx(n) < N1, then the warp sums its lanes.  A single pass over all
-// outputs is used: splitting the outputs over two passes (recomputing D) keeps
-// P = 8 spill-free but doubles the unrolled code and loses to instruction-cache
-// misses (measured 1.26 ms vs 0.76 ms at N = 1M, theta = 0.5).
+// N0 <= idx(n) < N1, then the warp sums its lanes.  At P = 8 the outputs are
+// split over two launches of this pass (each recomputing D): one kernel with
+// the whole unrolled contraction stalls on instruction-cache misses (0.76 ms
+// at N = 1M, theta = 0.5), two passes in one kernel are worse (1.26 ms: both
+// bodies compete for the cache), two launches of half the body each take
+// 0.65 ms in total, three or more launches lose to the repeated D (0.82+ ms).
 // ---------------------------------------------------------------------------
 template <int P, int N0, int N1>
 __device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, const int *level, const float4 *geom,
@@ -302,14 +305,13 @@ __device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, 
         for (int i = T + lane; i < TP; i += 32) dst[i] = 0.0f;
 }
 
-template <int P>
+template <int P, int N0, int N1>
 __global__ void __launch_bounds__(128) k_m2l(int ncells, const int *off, const int *src, const int *level,
                                              const float4 *geom, const float *M, float *L)
 {
-    constexpr int T = MI<P>::T;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= ncells) return;
-    m2l_pass<P, 0, T>(t, off, src, level, geom, M, L);
+    m2l_pass<P, N0, N1>(t, off, src, level, geom, M, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,12 +419,35 @@ template <int P> static int adjoint_upward_impl(Handle &h, const float *dphi, co
     return m2m_levels<P>(h, h.Ma.as<float>());
 }
 
+#ifndef FMM_M2L_KERNELS
+#define FMM_M2L_KERNELS 2
+#endif
+
+template <int P, int S, int I> struct M2LSlice {   // outputs [lo, hi) of launch I of S, multiples of 4
+    static constexpr int T = MI<P>::T;
+    static constexpr int lo = I == 0 ? 0 : ((T * I / S + 3) & ~3);
+    static constexpr int hi = I + 1 == S ? T : ((T * (I + 1) / S + 3) & ~3);
+};
+
+template <int P, int S, int I> static void m2l_slice_launch(Handle &h, int nc, const float *M, float *L)
+{
+    if constexpr (I < S) {
+        ++h.launches;
+        k_m2l<P, M2LSlice<P, S, I>::lo, M2LSlice<P, S, I>::hi><<<ceil_div((int64_t)nc * 32, 128), 128, 0, h.stream>>>(
+            nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), M, L);
+        m2l_slice_launch<P, S, I + 1>(h, nc, M, L);
+    }
+}
+
+// At high order the outputs are split over S launches, each recomputing the
+// kernel derivatives and running 1/S of the unrolled contraction: the extra
+// derivative work costs less than the instruction-cache misses of the whole
+// contraction in one kernel.
 template <int P> static int m2l_impl(Handle &h, const float *M, float *L)
 {
     const int nc = (int)h.ncells;
-    ++h.launches;
-    k_m2l<P><<<ceil_div((int64_t)nc * 32, 128), 128, 0, h.stream>>>(nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(),
-                                                                    h.c_level.as<int>(), h.c_geom.as<float4>(), M, L);
+    constexpr int S = P >= 8 ? FMM_M2L_KERNELS : 1;
+    m2l_slice_launch<P, S, 0>(h, nc, M, L);
     FMM_CHECK_LAUNCH("m2l");
     return FMM_OK;
 }
