@@ -140,19 +140,18 @@ int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, 
 // ---------------------------------------------------------------------------
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsRounds = 16;
-constexpr int kRsTile = kRsThreads * kRsRounds;   // 4096 keys per tile
+constexpr int kRsMaxRounds = 16;   // a tile is kRsThreads x rounds keys, rounds <= 16 (4096 keys)
 
 template <class K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *keys, int64_t n, int shift, int ntiles,
-                                                           unsigned *hist)
+                                                           int rounds, unsigned *hist)
 {
     __shared__ unsigned cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    const int64_t base = (int64_t)blockIdx.x * rounds * kRsThreads;
 #pragma unroll 4
-    for (int r = 0; r < kRsRounds; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         int64_t i = base + r * kRsThreads + threadIdx.x;
         if (i < n) atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 0xffu], 1u);
     }
@@ -162,8 +161,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *keys, int64_
 
 template <class K, bool kVals>
 __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *keys, const unsigned *vals, int64_t n,
-                                                           int shift, int ntiles, const unsigned *offsets,
-                                                           K *keys_out, unsigned *vals_out)
+                                                           int shift, int ntiles, int rounds,
+                                                           const unsigned *offsets, K *keys_out, unsigned *vals_out)
 {
     __shared__ unsigned s_base[256];
     __shared__ unsigned s_cnt[kRsWarps][256];
@@ -172,8 +171,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *keys, const 
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) s_cnt[w][t] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-    for (int r = 0; r < kRsRounds; ++r) {
+    const int64_t base = (int64_t)blockIdx.x * rounds * kRsThreads;
+    for (int r = 0; r < rounds; ++r) {
         const int64_t i = base + r * kRsThreads + t;
         const bool valid = i < n;
         K key = valid ? keys[i] : (K)0;
@@ -214,24 +213,27 @@ static int radix_sort_impl(Handle &h, K *&keys, K *&keys_alt, unsigned *&vals, u
         set_error("radix sort: more than 2^32 keys");
         return FMM_ERR_ARG;
     }
-    const int ntiles = ceil_div(n, kRsTile);
+    // tiles small enough that the grid covers the SMs about four times over
+    // (latency-bound kernels), at most 16 rounds of 256 keys
+    const int rounds = (int)std::max<int64_t>(1, std::min<int64_t>(kRsMaxRounds, n / ((int64_t)kRsThreads * 4 * h.num_sms)));
+    const int ntiles = ceil_div(n, (int64_t)rounds * kRsThreads);
     const int64_t nh = (int64_t)256 * ntiles;
     FMM_TRY(h.sort_hist.reserve((size_t)nh * 2 * sizeof(unsigned)));
     unsigned *hist = h.sort_hist.as<unsigned>();
     unsigned *offs = hist + nh;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         ++h.launches;
-        k_rs_upsweep<K><<<ntiles, kRsThreads, 0, h.stream>>>(keys, n, shift, ntiles, hist);
+        k_rs_upsweep<K><<<ntiles, kRsThreads, 0, h.stream>>>(keys, n, shift, ntiles, rounds, hist);
         FMM_CHECK_LAUNCH("radix upsweep");
         FMM_TRY(scan_exclusive_u32(h, hist, offs, nh, nullptr));
         if (with_vals) {
             ++h.launches;
-            k_rs_scatter<K, true><<<ntiles, kRsThreads, 0, h.stream>>>(keys, vals, n, shift, ntiles, offs, keys_alt,
-                                                                     vals_alt);
+            k_rs_scatter<K, true><<<ntiles, kRsThreads, 0, h.stream>>>(keys, vals, n, shift, ntiles, rounds, offs,
+                                                                     keys_alt, vals_alt);
         } else {
             ++h.launches;
-            k_rs_scatter<K, false><<<ntiles, kRsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ntiles, offs,
-                                                                      keys_alt, nullptr);
+            k_rs_scatter<K, false><<<ntiles, kRsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ntiles, rounds,
+                                                                      offs, keys_alt, nullptr);
         }
         FMM_CHECK_LAUNCH("radix scatter");
         K *tk = keys;
