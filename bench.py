@@ -532,7 +532,7 @@ def run_ours(a):
     achieved = pairs * FLOPS_PER_PAIR / (p2p_mean * 1e-3) / 1e12
     traffic = p2p_traffic(a)
 
-    # fmm_evaluate alone on the built tree (the paper's and the survey's
+    # fmm_evaluate alone on the built tree (the paper's
     # "FMM evals/s": tree construction excluded); reported beside the build +
     # evaluate step of `value`
     ms_eval_only = time_steps(torch, stream, lambda: h.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)

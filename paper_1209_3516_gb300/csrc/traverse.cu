@@ -351,7 +351,7 @@ int build_lists(Handle &h)
             h.n_p2p = 1;
             break;
         }
-        // the pair (root, root) seeds round 0
+        // the pair (root, root) is the frontier of seeding round 0
         h.pinned->ctr = TravCounters();
         h.pinned->ctr.round_count[0] = 1;
         int2 root = make_int2(0, 0);
