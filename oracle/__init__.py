@@ -70,6 +70,7 @@ def lib():
             L.orc_evaluate.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p, _dp, _dp]
             L.orc_evaluate.restype = ctypes.c_int
             L.orc_backward.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_int64, _i64p, _dp, _dp]
+            L.orc_set_hybrid.argtypes = [ctypes.c_void_p, ctypes.c_int64]
             L.orc_backward.restype = ctypes.c_int
             for name in ("orc_ncells", "orc_nm2l", "orc_np2p"):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
@@ -226,11 +227,13 @@ def direct_backward(x, q, dphi=None, dgrad=None, targets=None):
 class FMM:
     """Oracle FMM: tree + dual tree traversal + FP64 Cartesian Taylor evaluation."""
 
-    def __init__(self, N: int, P: int, theta: float, ncrit: int):
+    def __init__(self, N: int, P: int, theta: float, ncrit: int, hybrid_min_pairs: int = -1):
         self._h = lib().orc_create(int(N), int(P), float(theta), int(ncrit))
         if not self._h:
             raise ValueError("oracle rejected N=%r P=%r theta=%r ncrit=%r" % (N, P, theta, ncrit))
         self.N, self.P, self.theta, self.ncrit = int(N), int(P), float(theta), int(ncrit)
+        # the M2L / P2P hybrid at the leaves (-1: Algorithm 4 as printed)
+        lib().orc_set_hybrid(self._h, int(hybrid_min_pairs))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -573,6 +573,7 @@ typedef struct orc_fmm {
     int64_t N;
     int P, ncrit;
     float theta;
+    int64_t hybrid_min_pairs;   /* < 0: Algorithm 4 as printed; else the M2L / P2P hybrid (orc_interact) */
     orc_mindex mi;
     /* normalisation */
     double centre[3], h;
@@ -618,6 +619,7 @@ orc_fmm *orc_create(int64_t N, int P, float theta, int ncrit)
     f->P = P;
     f->theta = theta;
     f->ncrit = ncrit;
+    f->hybrid_min_pairs = -1;
     orc_mindex_init(&f->mi, P);
     if (orc_mindex_terms(&f->mi)) { orc_mindex_free(&f->mi); free(f); return NULL; }
     return f;
@@ -768,12 +770,26 @@ static int orc_mac(const orc_fmm *f, int64_t A, int64_t B)
 }
 
 /* Algorithm 4, Interact(A, B). */
+/*
+ * Algorithm 4: both leaves -> P2P (checked before the MAC, as printed); else
+ * MAC -> M2L; else push.  With hybrid_min_pairs >= 0 (the M2L / P2P hybrid
+ * the paper describes for exaFMM, Sec. 2: the choice between the two kernels
+ * at the leaves is tuned): a leaf pair that passes the MAC and holds at least
+ * hybrid_min_pairs particle pairs (n_A n_B) is an M2L pair instead.
+ */
 static int orc_interact(orc_fmm *f, orc_pairvec *stack, int64_t A, int64_t B)
 {
-    if (orc_is_leaf(f, A) && orc_is_leaf(f, B)) return orc_pv_push(&f->p2p, A, B);
+    if (orc_is_leaf(f, A) && orc_is_leaf(f, B)) {
+        if (f->hybrid_min_pairs >= 0 && f->pcnt[A] * f->pcnt[B] >= f->hybrid_min_pairs && orc_mac(f, A, B))
+            return orc_pv_push(&f->m2l, A, B);
+        return orc_pv_push(&f->p2p, A, B);
+    }
     if (orc_mac(f, A, B)) return orc_pv_push(&f->m2l, A, B);
     return orc_pv_push(stack, A, B);
 }
+
+/* The M2L / P2P hybrid for the next build: min_pairs < 0 turns it off. */
+void orc_set_hybrid(orc_fmm *f, int64_t min_pairs) { f->hybrid_min_pairs = min_pairs; }
 
 /*
  * Algorithm 3, dual tree traversal from the pair (root, root).

@@ -159,3 +159,21 @@ def test_table3_soft_anchor():
         assert es.max() / es.min() < 2.5, (err, es)
     ratio = np.mean(by_row[1e-3]) / np.mean(by_row[1e-4])
     assert 4.0 < ratio < 25.0, ratio
+
+
+def test_hybrid_accuracy_stays_within_the_mac_bound():
+    # moving MAC-passing leaf pairs from P2P to M2L keeps the error of the same
+    # order (the MAC bounds every M2L pair) and it still falls with P
+    N = 20000
+    x, q = inputs.uniform_cube(N, 2900)
+    pd, gd = oracle.direct(x, q)
+    errs = {}
+    for P in (4, 6, 8):
+        for hyb in (-1, 0):
+            pr, gr = oracle.FMM(N, P, 0.5, 32, hybrid_min_pairs=hyb).build(x).evaluate(q)
+            errs[(P, hyb)] = (np.linalg.norm(pr - pd) / np.linalg.norm(pd), np.linalg.norm(gr - gd) / np.linalg.norm(gd))
+    for P in (4, 6, 8):
+        assert errs[(P, 0)][0] <= 5 * errs[(P, -1)][0] and errs[(P, 0)][1] <= 5 * errs[(P, -1)][1], errs
+    assert errs[(4, 0)][1] > errs[(6, 0)][1] > errs[(8, 0)][1]
+    pr0, gr0 = oracle.FMM(N, 4, 0.0, 32, hybrid_min_pairs=0).build(x).evaluate(q)
+    assert np.linalg.norm(pr0 - pd) / np.linalg.norm(pd) < 1e-13   # theta = 0: the MAC never passes

@@ -110,8 +110,9 @@ def test_cell_geometry():
         assert B <= np.sqrt(3) * half * (1 + 1e-6)
 
 
-def _recursive_dtt(c, theta):
-    """Algorithms 3 and 4 written as a recursion over (A, B) pairs."""
+def _recursive_dtt(c, theta, hybrid_min_pairs=-1):
+    """Algorithms 3 and 4 written as a recursion over (A, B) pairs (with the
+    M2L / P2P hybrid at the leaves when hybrid_min_pairs >= 0)."""
     leaf = c["nchild"] == 0
     child = {}
     for i, p in enumerate(c["parent"]):
@@ -128,7 +129,11 @@ def _recursive_dtt(c, theta):
 
     def interact(A, B):
         if leaf[A] and leaf[B]:
-            p2p.append((A, B))
+            n = int(c["pcnt"][A]) * int(c["pcnt"][B])
+            if hybrid_min_pairs >= 0 and n >= hybrid_min_pairs and mac(A, B):
+                m2l.append((A, B))
+            else:
+                p2p.append((A, B))
         elif mac(A, B):
             m2l.append((A, B))
         else:
@@ -207,3 +212,43 @@ def test_list_growth_with_theta():
     assert np.all(np.diff(sizes[:, 1]) < 0)  # fewer near-field pairs as theta grows
     total_near = sizes[:, 1]
     assert total_near[0] / total_near[-1] > 2.0
+
+
+@pytest.mark.parametrize("N,ncrit,theta,hybrid", [(800, 8, 0.4, 0), (1500, 16, 0.6, 100), (1500, 8, 0.5, 40),
+                                                  (2000, 12, 0.5, 10 ** 9)])
+def test_hybrid_traversal_matches_recursive_definition(N, ncrit, theta, hybrid):
+    # the M2L / P2P hybrid at the leaves: a MAC-passing leaf pair with at least
+    # `hybrid` particle pairs is M2L; a threshold above every leaf pair gives the
+    # lists of Algorithm 4 as printed
+    x, _ = inputs.uniform_cube(N, 33) if hybrid != 40 else inputs.plummer(N, 34)
+    f = oracle.FMM(N, 4, theta, ncrit, hybrid_min_pairs=hybrid).build(x)
+    c = f.cells()
+    m2l_i, p2p_i = f.lists_idx()
+    m2l_r, p2p_r = _recursive_dtt(c, theta, hybrid)
+    assert _as_set(m2l_i, c["canon"]) == _as_set(m2l_r, c["canon"])
+    assert _as_set(p2p_i, c["canon"]) == _as_set(p2p_r, c["canon"])
+    if hybrid == 10 ** 9:
+        m0, p0 = oracle.FMM(N, 4, theta, ncrit).build(x).lists_idx()
+        assert _as_set(m0, c["canon"]) == _as_set(m2l_i, c["canon"])
+        assert _as_set(p0, c["canon"]) == _as_set(p2p_i, c["canon"])
+    else:
+        leaf = c["nchild"] == 0
+        assert any(leaf[A] and leaf[B] for A, B in m2l_i)   # some leaf pairs moved to M2L
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5])
+def test_hybrid_covers_every_particle_pair_exactly_once(theta):
+    N, ncrit = 900, 10
+    x, _ = inputs.uniform_cube(N, 42)
+    f = oracle.FMM(N, 4, theta, ncrit, hybrid_min_pairs=0).build(x)
+    c = f.cells()
+    m2l, p2p = f.lists_idx()
+    cover = np.zeros((N, N), dtype=np.int32)
+    for A, B in np.concatenate([m2l, p2p]):
+        a0, a1 = c["pbeg"][A], c["pbeg"][A] + c["pcnt"][A]
+        b0, b1 = c["pbeg"][B], c["pbeg"][B] + c["pcnt"][B]
+        cover[a0:a1, b0:b1] += 1
+    assert np.all(cover == 1)
+    for A, B in m2l:
+        R = np.linalg.norm(c["centre"][A].astype(np.float64) - c["centre"][B])
+        assert theta * R >= (float(c["radius"][A]) + float(c["radius"][B])) * (1 - 1e-6)
