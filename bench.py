@@ -51,10 +51,14 @@ def parse():
     ap.add_argument("--ncrit", type=int, default=64)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "plummer"])
     ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
+    ap.add_argument("--hybrid", type=int, default=None,
+                    help="M2L / P2P hybrid at the leaves: MAC-passing leaf pairs with at least this many "
+                         "particle pairs go to M2L (default: Algorithm 4 as printed)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="all",
-                    choices=["all", "none", "adaptive", "differentiated", "batched", "systems", "ncrit"],
+                    choices=["all", "none", "adaptive", "differentiated", "batched", "systems", "ncrit",
+                             "hybrid"],
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
@@ -75,6 +79,8 @@ def config(a):
     return {"workload": "%s N=%d, P=%d, theta=%.2f, ncrit=%d, potential+gradient, one charge vector%s"
                         % (what, a.N, a.P, a.theta, a.ncrit, ", compensated P2P" if a.kahan else ""),
             "N": a.N, "P": a.P, "theta": a.theta, "ncrit": a.ncrit, "dist": a.dist, "kahan": a.kahan,
+            "hybrid_min_pairs": a.hybrid,
+            "traversal": "Algorithm 4 as printed" if a.hybrid is None else "M2L / P2P hybrid at the leaves",
             "step": "fmm_build + fmm_evaluate",
             "l2": "flushed before every timed step (256 MiB write)"}
 
@@ -129,7 +135,7 @@ def p2p_traffic(a):
         pj = json.load(open(prof))
         if (pj.get("N"), pj.get("P"), pj.get("theta"), pj.get("ncrit")) != (a.N, a.P, a.theta, a.ncrit):
             return None
-        if (pj.get("dist", "uniform"), pj.get("kahan", False)) != (a.dist, a.kahan):
+        if (pj.get("dist", "uniform"), pj.get("kahan", False), pj.get("hybrid")) != (a.dist, a.kahan, a.hybrid):
             return None
         h = hashlib.sha256()
         for f in pj["sources"]:
@@ -306,7 +312,41 @@ def run_variants(torch, stream, flush, which="all", batch_n=1048576):
         out.update(variant_systems(torch, stream, flush))
     if which in ("all", "ncrit"):
         out.update(variant_ncrit(torch))
+    if which in ("all", "hybrid"):
+        out.update(variant_hybrid(torch, stream, flush))
     return out
+
+
+def variant_hybrid(torch, stream, flush):
+    """The M2L / P2P hybrid at the leaves on the N = 1M uniform workload (P = 8,
+    theta = 0.5, ncrit = 64): fmm_tune_hybrid over the M2L threshold (-1 is
+    Algorithm 4 as printed), then the chosen setting timed like the main line."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    N, P, theta, ncrit = 1048576, 8, 0.5, 64
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    best, ms = fmm.tune_hybrid(xd, qd, P, theta, ncrit, candidates=(-1, 0, 256, 512, 1024, 2048), reps=3)
+    phi = torch.empty(N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(N, 3, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, hyb in (("algorithm_4", None), ("hybrid", best)):
+        h = fmm.FMM(N, P, theta, ncrit, hybrid=hyb, timing=True)
+
+        def step():
+            h.build(xd)
+            h.evaluate(qd, phi=phi, grad=grad)
+        t = time_steps(torch, stream, step, 20, 3, flush)
+        st = h.stats()
+        out[name] = {"evals_per_s": 1e3 / t, "ms": t, "n_m2l": st["n_m2l"], "n_p2p": st["n_p2p"],
+                     "p2p_pairs": st["p2p_pairs"], "phases_ms": st["ms_phase"]}
+        h.close()
+    return {"hybrid_1m": {
+        "workload": "uniform cube N=1048576, P=8, theta=0.5, ncrit=64, build + evaluate, L2 flushed: "
+                    "Algorithm 4 as printed vs the M2L / P2P hybrid at the leaves (threshold tuned)",
+        "tuned_min_pairs": best, "tune_ms": {str(k): v for k, v in ms.items()},
+        "algorithm_4": out["algorithm_4"], "hybrid": out["hybrid"],
+        "hybrid_vs_algorithm_4": out["algorithm_4"]["ms"] / out["hybrid"]["ms"]}}
 
 
 def variant_ncrit(torch):
@@ -483,7 +523,7 @@ def run_ours(a):
     phi = torch.empty(a.N, dtype=torch.float32, device="cuda")
     grad = torch.empty(a.N, 3, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, kahan=a.kahan, timing=True)
+    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, kahan=a.kahan, timing=True, hybrid=a.hybrid)
 
     def step():
         h.build(xd)

@@ -264,6 +264,26 @@ int fmm_multi_info(fmm_multi *m, struct fmm_multi_info *info);
 int fmm_multi_destroy(fmm_multi *m);
 
 /*
+ * fmm_set_hybrid -- the M2L / P2P hybrid at the leaves, for the next fmm_build.
+ * Algorithm 4 sends a pair of leaves to P2P before looking at the MAC; with
+ * min_pairs >= 0 a leaf pair that passes the MAC and holds at least min_pairs
+ * particle pairs (n_A n_B) goes to M2L instead (the choice between the two
+ * kernels at the leaves that the paper's exaFMM tunes, Sec. 2).  min_pairs < 0
+ * (the default) keeps Algorithm 4 as printed.  The accuracy is still bounded by
+ * the MAC; the lists change, so the oracle must be run with the same setting.
+ */
+int fmm_set_hybrid(fmm_handle *h, int64_t min_pairs);
+
+/*
+ * fmm_tune_hybrid -- like fmm_tune_ncrit, over candidate min_pairs values of the
+ * hybrid (HOST array; a negative value is Algorithm 4 as printed) at one ncrit:
+ * the fastest build + evaluate goes to *best, the medians to ms_out.
+ */
+int fmm_tune_hybrid(int64_t N, int P, float theta, int ncrit, const double *x, const float *q,
+                    const int64_t *candidates, int ncand, int reps, const fmm_options *opt, int64_t *best,
+                    double *ms_out);
+
+/*
  * fmm_tune_ncrit -- the leaf size at which the evaluation is fastest for this
  * input: the balance between M2L (more, smaller cells) and P2P (fewer, larger
  * leaves) that the paper's auto-tuned hybrid selects by timing (Sec. 2, the

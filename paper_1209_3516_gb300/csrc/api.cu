@@ -361,6 +361,60 @@ int fmm_backward(fmm_handle *w, const float *dphi, const float *dgrad, float *dq
     return FMM_OK;
 }
 
+int fmm_set_hybrid(fmm_handle *w, int64_t min_pairs)
+{
+    if (!w) {
+        set_error("fmm_set_hybrid: null handle");
+        return FMM_ERR_ARG;
+    }
+    w->h.hybrid_min_pairs = min_pairs < 0 ? -1 : min_pairs;
+    w->h.built = false;   // the lists change: the next evaluate needs a build
+    return FMM_OK;
+}
+
+// Median device time (ms) of build + evaluate over reps runs after one warm-up.
+static int time_config(int64_t N, int P, float theta, int ncrit, int64_t hybrid, const double *x, const float *q,
+                       int reps, const fmm_options *opt, double *ms_out)
+{
+    fmm_handle *w = nullptr;
+    fmm_options o = opt ? *opt : fmm_options{nullptr, -1, 0u};
+    o.flags &= ~FMM_FLAG_TIMING;
+    FMM_TRY(fmm_create(&w, N, P, theta, ncrit, &o));
+    Handle &h = w->h;
+    h.hybrid_min_pairs = hybrid;
+    int rc = FMM_OK;
+    DevBuf phi, grad;
+    std::vector<float> times;
+    {
+        DeviceGuard guard(h.device);
+        rc = phi.reserve((size_t)N * sizeof(float));
+        if (rc == FMM_OK) rc = grad.reserve((size_t)N * 3 * sizeof(float));
+        if (rc == FMM_OK && !h.events_ready) {
+            set_error("autotuner: no CUDA events");
+            rc = FMM_ERR_CUDA;
+        }
+        for (int r = 0; r <= reps && rc == FMM_OK; ++r) {   // r = 0: warm-up
+            // do_build records the build's start event and synchronises at its end
+            rc = do_build(h, x);
+            if (rc == FMM_OK) rc = do_evaluate(h, q, phi.as<float>(), grad.as<float>());
+            if (rc == FMM_OK) {
+                cudaEventRecord(h.ev[2 * kPhases + 1], h.stream);
+                cudaEventSynchronize(h.ev[2 * kPhases + 1]);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, h.ev[2 * kPhases], h.ev[2 * kPhases + 1]);
+                if (r > 0) times.push_back(ms);
+            }
+        }
+        phi.release();
+        grad.release();
+    }
+    fmm_destroy(w);
+    if (rc != FMM_OK) return rc;
+    std::sort(times.begin(), times.end());
+    *ms_out = times[times.size() / 2];
+    return FMM_OK;
+}
+
 int fmm_tune_ncrit(int64_t N, int P, float theta, const double *x, const float *q, const int *candidates,
                    int ncand, int reps, const fmm_options *opt, int *best, double *ms_out)
 {
@@ -371,44 +425,33 @@ int fmm_tune_ncrit(int64_t N, int P, float theta, const double *x, const float *
     double best_ms = 1e300;
     *best = candidates[0];
     for (int k = 0; k < ncand; ++k) {
-        fmm_handle *w = nullptr;
-        fmm_options o = opt ? *opt : fmm_options{nullptr, -1, 0u};
-        o.flags &= ~FMM_FLAG_TIMING;
-        FMM_TRY(fmm_create(&w, N, P, theta, candidates[k], &o));
-        Handle &h = w->h;
-        int rc = FMM_OK;
-        DevBuf phi, grad;
-        std::vector<float> times;
-        {
-            DeviceGuard guard(h.device);
-            rc = phi.reserve((size_t)N * sizeof(float));
-            if (rc == FMM_OK) rc = grad.reserve((size_t)N * 3 * sizeof(float));
-            for (int r = 0; r <= reps && rc == FMM_OK; ++r) {   // r = 0: warm-up
-                if (h.events_ready) cudaEventRecord(h.ev[2 * kPhases], h.stream);
-                rc = do_build(h, x);   // synchronises; its events bracket the build
-                if (rc == FMM_OK) rc = do_evaluate(h, q, phi.as<float>(), grad.as<float>());
-                if (rc == FMM_OK && h.events_ready) {
-                    cudaEventRecord(h.ev[2 * kPhases + 1], h.stream);
-                    cudaEventSynchronize(h.ev[2 * kPhases + 1]);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, h.ev[2 * kPhases], h.ev[2 * kPhases + 1]);
-                    if (r > 0) times.push_back(ms);
-                }
-            }
-            if (rc == FMM_OK && !h.events_ready) {
-                set_error("fmm_tune_ncrit: no CUDA events");
-                rc = FMM_ERR_CUDA;
-            }
-            phi.release();
-            grad.release();
+        double ms = 0.0;
+        FMM_TRY(time_config(N, P, theta, candidates[k], -1, x, q, reps, opt, &ms));
+        if (ms_out) ms_out[k] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = candidates[k];
         }
-        fmm_destroy(w);
-        if (rc != FMM_OK) return rc;
-        std::sort(times.begin(), times.end());
-        const double med = times[times.size() / 2];
-        if (ms_out) ms_out[k] = med;
-        if (med < best_ms) {
-            best_ms = med;
+    }
+    return FMM_OK;
+}
+
+int fmm_tune_hybrid(int64_t N, int P, float theta, int ncrit, const double *x, const float *q,
+                    const int64_t *candidates, int ncand, int reps, const fmm_options *opt, int64_t *best,
+                    double *ms_out)
+{
+    if (!x || !q || !candidates || ncand < 1 || reps < 1 || !best) {
+        set_error("fmm_tune_hybrid: null argument or empty candidate list");
+        return FMM_ERR_ARG;
+    }
+    double best_ms = 1e300;
+    *best = candidates[0];
+    for (int k = 0; k < ncand; ++k) {
+        double ms = 0.0;
+        FMM_TRY(time_config(N, P, theta, ncrit, candidates[k] < 0 ? -1 : candidates[k], x, q, reps, opt, &ms));
+        if (ms_out) ms_out[k] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
             *best = candidates[k];
         }
     }

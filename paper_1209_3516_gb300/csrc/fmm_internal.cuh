@@ -87,6 +87,7 @@ struct Handle {
     int64_t N = 0;
     int P = 0, TP = 0, ncrit = 0;
     float theta = 0.f;
+    int64_t hybrid_min_pairs = -1;   // M2L / P2P hybrid at the leaves (< 0: off)
     unsigned flags = 0;
     int device = 0;
     int num_sms = 0;

@@ -48,24 +48,37 @@ constexpr int kMaxStackPasses = 256;
 struct Cell {
     float4 g;   // centre, radius
     int2 k;     // first child, child count (0 = leaf)
+    int n;      // particles
 };
 
-__device__ __forceinline__ Cell load_cell(const float4 *geom, const int2 *kids, int c)
+__device__ __forceinline__ Cell load_cell(const float4 *geom, const int2 *kids, const int *pcnt, int c)
 {
     Cell r;
     r.g = geom[c];
     r.k = kids[c];
+    r.n = pcnt[c];
     return r;
 }
 
-// Algorithm 4 outcome for the pair (a, b): 1 = P2P, 2 = M2L, 3 = push.
-__device__ __forceinline__ int interact(const Cell &a, const Cell &b, float theta)
+__device__ __forceinline__ bool mac(const Cell &a, const Cell &b, float theta)
 {
-    if (a.k.y == 0 && b.k.y == 0) return 1;
     const float dx = __fsub_rn(a.g.x, b.g.x), dy = __fsub_rn(a.g.y, b.g.y), dz = __fsub_rn(a.g.z, b.g.z);
     const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
     const float R = __fsqrt_rn(r2);
-    return __fmul_rn(theta, R) > __fadd_rn(a.g.w, b.g.w) ? 2 : 3;
+    return __fmul_rn(theta, R) > __fadd_rn(a.g.w, b.g.w);
+}
+
+// Algorithm 4 outcome for the pair (a, b): 1 = P2P, 2 = M2L, 3 = push.  Both
+// leaves go to P2P before the MAC is looked at, unless the M2L / P2P hybrid is
+// on (hybrid_min >= 0): then a leaf pair that passes the MAC and holds at least
+// hybrid_min particle pairs is an M2L pair.
+__device__ __forceinline__ int interact(const Cell &a, const Cell &b, float theta, long long hybrid_min)
+{
+    if (a.k.y == 0 && b.k.y == 0) {
+        if (hybrid_min >= 0 && (long long)a.n * (long long)b.n >= hybrid_min && mac(a, b, theta)) return 2;
+        return 1;
+    }
+    return mac(a, b, theta) ? 2 : 3;
 }
 
 // Algorithm 3 split rule: true = split the target A.
@@ -77,7 +90,9 @@ __device__ __forceinline__ bool split_target(const Cell &A, const Cell &B)
 struct TravArgs {
     const float4 *geom;
     const int2 *kids;
+    const int *pcnt;
     float theta;
+    long long hybrid_min;   // < 0: Algorithm 4 as printed
     int2 *m2l;
     unsigned long long m2l_cap;
     int2 *p2p;
@@ -92,18 +107,18 @@ struct TravArgs {
 // Child pair j (0..7) of a popped pair; returns false when the split cell has fewer children.
 __device__ __forceinline__ bool child_pair(const TravArgs &a, int2 pr, int j, int2 &np, Cell &ca, Cell &cb)
 {
-    const Cell A = load_cell(a.geom, a.kids, pr.x);
-    const Cell B = load_cell(a.geom, a.kids, pr.y);
+    const Cell A = load_cell(a.geom, a.kids, a.pcnt, pr.x);
+    const Cell B = load_cell(a.geom, a.kids, a.pcnt, pr.y);
     if (split_target(A, B)) {
         if (j >= A.k.y) return false;
         np = make_int2(A.k.x + j, pr.y);
-        ca = load_cell(a.geom, a.kids, np.x);
+        ca = load_cell(a.geom, a.kids, a.pcnt, np.x);
         cb = B;
     } else {
         if (j >= B.k.y) return false;
         np = make_int2(pr.x, B.k.x + j);
         ca = A;
-        cb = load_cell(a.geom, a.kids, np.y);
+        cb = load_cell(a.geom, a.kids, a.pcnt, np.y);
     }
     return true;
 }
@@ -125,7 +140,7 @@ __global__ void k_dtt_round(const int2 *front, const unsigned long long *nfront_
         int2 np = make_int2(0, 0);
         if (t < total) {
             Cell ca, cb;
-            if (child_pair(a, front[t >> 3], (int)(t & 7ull), np, ca, cb)) kind = interact(ca, cb, a.theta);
+            if (child_pair(a, front[t >> 3], (int)(t & 7ull), np, ca, cb)) kind = interact(ca, cb, a.theta, a.hybrid_min);
         }
         warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
         warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
@@ -176,7 +191,7 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
         __syncwarp();   // every popped entry is read before pushes overwrite the slots
         if (p < npop) {
             Cell ca, cb;
-            if (child_pair(a, pr, j, np, ca, cb)) kind = interact(ca, cb, a.theta);
+            if (child_pair(a, pr, j, np, ca, cb)) kind = interact(ca, cb, a.theta, a.hybrid_min);
         }
         warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
         warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
@@ -333,7 +348,9 @@ int build_lists(Handle &h)
         TravArgs a;
         a.geom = h.c_geom.as<float4>();
         a.kids = h.c_kids.as<int2>();
+        a.pcnt = h.c_pcnt.as<int>();
         a.theta = h.theta;
+        a.hybrid_min = h.hybrid_min_pairs;
         a.m2l = h.m2l_raw.as<int2>();
         a.m2l_cap = h.m2l_cap;
         a.p2p = h.p2p_raw.as<int2>();

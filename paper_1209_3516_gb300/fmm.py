@@ -97,6 +97,10 @@ def load():
     L.fmm_multi_evaluate.argtypes = [_vp, _vp, _vp, _vp]
     L.fmm_multi_info.argtypes = [_vp, ctypes.POINTER(_MultiInfo)]
     L.fmm_multi_destroy.argtypes = [_vp]
+    L.fmm_set_hybrid.argtypes = [_vp, ctypes.c_int64]
+    L.fmm_tune_hybrid.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_int, _vp, _vp,
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options),
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
     L.fmm_tune_ncrit.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_double)]
@@ -141,6 +145,23 @@ def tune_ncrit(x, q, P, theta, candidates=(16, 32, 48, 64, 96, 128), reps=3, str
     return best.value, {c: ms[i] for i, c in enumerate(candidates)}
 
 
+def tune_hybrid(x, q, P, theta, ncrit=64, candidates=(-1, 0, 256, 512, 1024, 2048), reps=3, stream=None):
+    """fmm_tune_hybrid: (best min_pairs, {min_pairs: median ms of build + evaluate}); -1 = Algorithm 4."""
+    import torch
+    N = x.shape[0]
+    xp = _dev_ptr(x, torch.float64, (N, 3), "x")
+    qp = _dev_ptr(q, torch.float32, (N,), "q")
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    opt = _Options(ctypes.c_void_p(stream.cuda_stream), x.device.index or 0, 0)
+    cand = (ctypes.c_int64 * len(candidates))(*candidates)
+    ms = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_int64()
+    _check(load().fmm_tune_hybrid(N, int(P), float(theta), int(ncrit), xp, qp, cand, len(candidates), int(reps),
+                                  ctypes.byref(opt), ctypes.byref(best), ms))
+    return best.value, {c: ms[i] for i, c in enumerate(candidates)}
+
+
 def energy_noalloc(q, phi, E, stream=None):
     """fmm_energy_noalloc: E[0] = 1/2 sum q phi into the caller's device double E (no allocation)."""
     import torch
@@ -157,7 +178,8 @@ def energy_noalloc(q, phi, E, stream=None):
 class FMM:
     """A handle: fmm_create(N, P, theta, ncrit) on the current CUDA device and stream."""
 
-    def __init__(self, N, P=4, theta=0.4, ncrit=64, kahan=False, timing=False, stream=None, device=None):
+    def __init__(self, N, P=4, theta=0.4, ncrit=64, kahan=False, timing=False, stream=None, device=None,
+                 hybrid=None):
         import torch
         L = load()
         if device is None:
@@ -172,6 +194,8 @@ class FMM:
         _check(L.fmm_create(ctypes.byref(h), int(N), int(P), float(theta), int(ncrit), ctypes.byref(opt)))
         self._h = h
         self.N, self.P, self.theta, self.ncrit = int(N), int(P), float(theta), int(ncrit)
+        if hybrid is not None:   # M2L / P2P hybrid at the leaves: minimum particle pairs for M2L
+            _check(L.fmm_set_hybrid(h, int(hybrid)))
         self.evaluations = 0   # fmm_evaluate calls so far (the adjoint differentiates the last one)
 
     def close(self):

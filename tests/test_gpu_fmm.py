@@ -32,10 +32,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-def run_gpu(torch, x, q, P, theta, ncrit, kahan=False):
+def run_gpu(torch, x, q, P, theta, ncrit, kahan=False, hybrid=None):
     from paper_1209_3516_gb300 import fmm
     N = x.shape[0]
-    h = fmm.FMM(N, P, theta, ncrit, kahan=kahan)
+    h = fmm.FMM(N, P, theta, ncrit, kahan=kahan, hybrid=hybrid)
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     qd = torch.from_numpy(q.astype(np.float32)).cuda()
     h.build(xd)
@@ -485,3 +485,62 @@ def test_plummer_4m_sweep(torch_cuda):
     for ncrit in (32, 64, 128):
         assert err[(8, ncrit)][1] < err[(4, ncrit)][1]   # the higher order is the more accurate
         assert err[(8, ncrit)][0] <= 1e-4 and err[(8, ncrit)][1] <= 1e-4
+
+
+
+HYBRID_CASES = [
+    # N, P, theta, ncrit, hybrid min pairs, kind
+    (16384, 8, 0.5, 64, 0, "u"),
+    (16384, 4, 0.4, 64, 512, "u"),
+    (20000, 6, 0.5, 32, 0, "p"),
+    (5001, 8, 0.5, 17, 100, "u"),
+]
+
+
+@pytest.mark.parametrize("N,P,theta,ncrit,hybrid,kind", HYBRID_CASES)
+def test_hybrid_parity_with_oracle(torch_cuda, N, P, theta, ncrit, hybrid, kind):
+    # the M2L / P2P hybrid at the leaves: same lists as the oracle run with the
+    # same threshold (bit-exact), potential and gradient within 1e-5
+    x, q = inputs.uniform_cube(N, 1700 + N) if kind == "u" else inputs.plummer(N, 1701 + N)
+    if kind == "p":
+        q = inputs.rng(1702 + N).random(N) * 2 - 1
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit, hybrid=hybrid)
+    ref = oracle.FMM(N, P, theta, ncrit, hybrid_min_pairs=hybrid).build(x)
+    check_structure(h, ref)
+    pr, gr = ref.evaluate(q32)
+    assert rel_l2(phi, pr) <= TOL, rel_l2(phi, pr)
+    assert rel_l2(grad, gr) <= TOL, rel_l2(grad, gr)
+    h.close()
+
+
+def test_tune_hybrid(torch_cuda):
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 30000
+    x, q = inputs.uniform_cube(N, 1800)
+    best, ms = fmm.tune_hybrid(torch.from_numpy(x).cuda(), torch.from_numpy(q.astype(np.float32)).cuda(), 8, 0.5,
+                               64, candidates=(-1, 0, 1024), reps=2)
+    assert best in ms and ms[best] == min(ms.values())
+
+
+@pytest.mark.slow
+def test_full_size_hybrid_1m(torch_cuda):
+    # the benchmark geometry with the hybrid on (every MAC-passing leaf pair to M2L):
+    # lists bit-exact against the oracle with the same rule, values on the sample
+    N, P, theta, ncrit = 1048576, 8, 0.5, 64
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    q32 = q.astype(np.float32).astype(np.float64)
+    h, phi, grad = run_gpu(torch_cuda, x, q32, P, theta, ncrit, hybrid=0)
+    ref = oracle.FMM(N, P, theta, ncrit, hybrid_min_pairs=0).build(x)
+    check_structure(h, ref)
+    t = inputs.sample_targets(N, 4096)
+    pr, gr = ref.evaluate(q32, t)
+    assert rel_l2(phi[t], pr) <= TOL and rel_l2(grad[t], gr) <= TOL
+    pd, gd = oracle.direct(x, q32, t)
+    st = h.stats()
+    e = (rel_l2(phi[t], pd), rel_l2(grad[t], gd))
+    print("hybrid N=1M P=8 theta=0.5: err vs direct phi %.2e grad %.2e; M2L %d P2P %d pairs %d"
+          % (e[0], e[1], st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
+    assert max(e) <= 1e-4
+    h.close()
