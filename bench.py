@@ -386,6 +386,10 @@ def variant_systems(torch, stream, flush):
     ms_m = time_steps(torch, stream, lambda: m.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)
     info = m.info()
     m.close()
+    mh = fmm.MultiFMM(sizes, P, theta, ncrit, hybrid=256)   # with the M2L / P2P hybrid at the leaves
+    mh.build(xd)
+    ms_mh = time_steps(torch, stream, lambda: mh.evaluate(qd, phi=phi, grad=grad), 20, 3, flush)
+    mh.close()
     hs, offs, off = [], [], 0
     for n in sizes:
         h = fmm.FMM(n, P, theta, ncrit)
@@ -404,8 +408,10 @@ def variant_systems(torch, stream, flush):
         "workload": "64 systems, N ~ lognormal in [1000, 200000] (total %d), uniform cube, charges U[-1,1), "
                     "P=8, theta=0.5, ncrit=64, trees built once; merged evaluation (one launch per operator) "
                     "replayed from a CUDA graph vs 64 plain fmm_evaluate calls" % Ntot,
-        "system_sets_per_s": {"plain_fp32_64_calls": 1e3 / ms_p, "merged_graph": 1e3 / ms_m},
-        "ms": {"plain_fp32_64_calls": ms_p, "merged_graph": ms_m}, "merged_vs_plain": ms_p / ms_m,
+        "system_sets_per_s": {"plain_fp32_64_calls": 1e3 / ms_p, "merged_graph": 1e3 / ms_m,
+                              "merged_graph_hybrid_256": 1e3 / ms_mh},
+        "ms": {"plain_fp32_64_calls": ms_p, "merged_graph": ms_m, "merged_graph_hybrid_256": ms_mh},
+        "merged_vs_plain": ms_p / ms_m,
         "graph_nodes": info["graph_nodes"], "p2p_targets_per_item": info["p2p_targets_per_item"],
         "autotune_p2p_ms": {"16_targets": info["tune_ms"][0], "8_targets": info["tune_ms"][1]},
         "p2p_pairs": info["p2p_pairs"]}}

@@ -258,6 +258,9 @@ int fmm_multi_build(fmm_multi *m, const double *x);
  */
 int fmm_multi_evaluate(fmm_multi *m, const float *q, float *phi, float *grad);
 
+/* fmm_multi_set_hybrid -- fmm_set_hybrid for every system, for the next fmm_multi_build. */
+int fmm_multi_set_hybrid(fmm_multi *m, int64_t min_pairs);
+
 /* fmm_multi_info -- sizes, the autotuner's timings and choice, the last replay's time (HOST *info). */
 int fmm_multi_info(fmm_multi *m, struct fmm_multi_info *info);
 

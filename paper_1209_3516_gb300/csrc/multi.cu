@@ -471,6 +471,17 @@ int fmm_multi_evaluate(fmm_multi *w, const float *q, float *phi, float *grad)
     return FMM_OK;
 }
 
+int fmm_multi_set_hybrid(fmm_multi *w, int64_t min_pairs)
+{
+    if (!w) {
+        set_error("fmm_multi_set_hybrid: null handle");
+        return FMM_ERR_ARG;
+    }
+    for (fmm_handle *h : w->m.sys) FMM_TRY(fmm_set_hybrid(h, min_pairs));
+    w->m.merged = false;   // the lists change: build again
+    return FMM_OK;
+}
+
 int fmm_multi_info(fmm_multi *w, struct fmm_multi_info *info)
 {
     if (!w || !info) {

@@ -97,6 +97,7 @@ def load():
     L.fmm_multi_evaluate.argtypes = [_vp, _vp, _vp, _vp]
     L.fmm_multi_info.argtypes = [_vp, ctypes.POINTER(_MultiInfo)]
     L.fmm_multi_destroy.argtypes = [_vp]
+    L.fmm_multi_set_hybrid.argtypes = [_vp, ctypes.c_int64]
     L.fmm_set_hybrid.argtypes = [_vp, ctypes.c_int64]
     L.fmm_tune_hybrid.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_int, _vp, _vp,
                                   ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options),
@@ -340,7 +341,7 @@ class MultiFMM:
     """fmm_multi_*: many independent systems (sizes N[s]) evaluated as one merged
     problem, replayed from a CUDA graph."""
 
-    def __init__(self, sizes, P=4, theta=0.4, ncrit=64, stream=None, device=None):
+    def __init__(self, sizes, P=4, theta=0.4, ncrit=64, stream=None, device=None, hybrid=None):
         import torch
         L = load()
         if device is None:
@@ -356,6 +357,8 @@ class MultiFMM:
         _check(L.fmm_multi_create(ctypes.byref(h), len(self.sizes), arr, int(P), float(theta), int(ncrit),
                                   ctypes.byref(opt)))
         self._h = h
+        if hybrid is not None:
+            _check(L.fmm_multi_set_hybrid(h, int(hybrid)))
 
     def close(self):
         if getattr(self, "_h", None):

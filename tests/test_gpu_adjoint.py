@@ -35,10 +35,10 @@ def upstream(N, seed):
     return g.standard_normal(N).astype(np.float32), g.standard_normal((N, 3)).astype(np.float32)
 
 
-def gpu_backward(torch, x, q32, a, b, P, theta, ncrit, kahan=False):
+def gpu_backward(torch, x, q32, a, b, P, theta, ncrit, kahan=False, hybrid=None):
     from paper_1209_3516_gb300 import fmm
     N = x.shape[0]
-    h = fmm.FMM(N, P, theta, ncrit, kahan=kahan)
+    h = fmm.FMM(N, P, theta, ncrit, kahan=kahan, hybrid=hybrid)
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     h.evaluate(torch.from_numpy(q32).cuda(), x=xd)
     ad = torch.from_numpy(a).cuda() if a is not None else None
@@ -148,6 +148,19 @@ def test_backward_with_compensated_forward(torch_cuda):
     h, dq, dx = gpu_backward(torch_cuda, x, q32, a, b, 4, 0.4, 64, kahan=True)
     rq, rx = oracle.FMM(N, 4, 0.4, 64).build(x).backward(q32.astype(np.float64), a.astype(np.float64),
                                                           b.astype(np.float64))
+    assert rel_l2(dq, rq) <= TOL and rel_l2(dx, rx) <= TOL
+    h.close()
+
+
+def test_backward_with_hybrid_lists(torch_cuda):
+    # the adjoint runs over whatever lists the traversal made, here the M2L / P2P hybrid's
+    N = 12000
+    x, q = inputs.uniform_cube(N, 3750)
+    q32 = q.astype(np.float32)
+    a, b = upstream(N, 3751)
+    h, dq, dx = gpu_backward(torch_cuda, x, q32, a, b, 6, 0.5, 32, hybrid=0)
+    rq, rx = oracle.FMM(N, 6, 0.5, 32, hybrid_min_pairs=0).build(x).backward(
+        q32.astype(np.float64), a.astype(np.float64), b.astype(np.float64))
     assert rel_l2(dq, rq) <= TOL and rel_l2(dx, rx) <= TOL
     h.close()
 

@@ -41,10 +41,10 @@ def systems(sizes, seed, plummer_every=0):
     return xs, qs
 
 
-def run_multi(torch, xs, qs, P, theta, ncrit):
+def run_multi(torch, xs, qs, P, theta, ncrit, hybrid=None):
     from paper_1209_3516_gb300 import fmm
     sizes = [x.shape[0] for x in xs]
-    m = fmm.MultiFMM(sizes, P, theta, ncrit)
+    m = fmm.MultiFMM(sizes, P, theta, ncrit, hybrid=hybrid)
     m.build(torch.from_numpy(np.concatenate(xs)).cuda())
     q = torch.from_numpy(np.concatenate(qs)).cuda()
     phi, grad = m.evaluate(q)
@@ -124,4 +124,20 @@ def test_multi_64_lognormal_systems(torch_cuda):
           "(tuned %.3f / %.3f ms); replay %.3f ms" % (sum(sizes), worst[0], worst[1], info["graph_nodes"],
                                                      info["p2p_targets_per_item"], info["tune_ms"][0],
                                                      info["tune_ms"][1], info["ms_evaluate"]))
+    m.close()
+
+
+def test_multi_with_hybrid(torch_cuda):
+    # the M2L / P2P hybrid applied to every system: each system against its own
+    # oracle run with the same rule
+    sizes = [6000, 300, 15000, 2500]
+    xs, qs = systems(sizes, 5300, plummer_every=2)
+    m, q, phi, grad = run_multi(torch_cuda, xs, qs, 8, 0.5, 32, hybrid=0)
+    phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+    off = 0
+    for x, qq in zip(xs, qs):
+        n = x.shape[0]
+        pr, gr = oracle.FMM(n, 8, 0.5, 32, hybrid_min_pairs=0).build(x).evaluate(qq.astype(np.float64))
+        assert rel_l2(phi[off:off + n], pr) <= TOL and rel_l2(grad[off:off + n], gr) <= TOL
+        off += n
     m.close()
