@@ -544,3 +544,25 @@ def test_full_size_hybrid_1m(torch_cuda):
           % (e[0], e[1], st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
     assert max(e) <= 1e-4
     h.close()
+
+
+@pytest.mark.slow
+def test_large_n_16m(torch_cuda):
+    # N = 16,777,216 uniform (P = 4, theta = 0.5): buffers regrow, 64-bit list keys,
+    # ~2e11 particle pairs; checked against the FP64 direct sum on 64 targets
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 1 << 24
+    x, q = inputs.uniform_cube(N, 1900)
+    q32 = q.astype(np.float32)
+    h = fmm.FMM(N, 4, 0.5, 64)
+    phi, grad = h.evaluate(torch.from_numpy(q32).cuda(), x=torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    t = inputs.sample_targets(N, 64)
+    pd, gd = oracle.direct(x, q32.astype(np.float64), t)
+    st = h.stats()
+    e = (rel_l2(phi.cpu().numpy()[t], pd), rel_l2(grad.cpu().numpy()[t], gd))
+    print("N=16M P=4 theta=0.5: err vs direct phi %.2e grad %.2e; cells %d levels %d M2L %d P2P %d pairs %d"
+          % (e[0], e[1], st["ncells"], st["nlevels"], st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
+    assert e[0] < 5e-3 and e[1] < 5e-3   # P = 4, theta = 0.5 accuracy (1.3e-3 / 6.4e-4 at N = 1M)
+    h.close()
