@@ -158,12 +158,15 @@ __global__ void k_m2m_batch(int lo, int n, const int *cbeg, const int *ccnt, con
 // every pair of the chunk with its multipole vector r.
 constexpr int kM2LBatchThreads = 64;   // two warps: 2 x 32 x (T + 1) floats of D fit static shared memory
 
-template <int P>
+// Outputs N0 <= idx(n) < N1 only (at P = 8 two launches split them, as for the
+// single-vector M2L: half the accumulators, no spills; multipole coefficients
+// that no output of the slice uses are not loaded).
+template <int P, int N0, int N1>
 __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, const int *off, const int *src,
                                                                 const int *level, const float4 *geom, const float *Mb,
                                                                 float *Lb)
 {
-    constexpr int T = MI<P>::T, TP = MI<P>::TP;
+    constexpr int T = MI<P>::T, TP = MI<P>::TP, NO = N1 - N0;
     constexpr int W = kM2LBatchThreads / 32;
     __shared__ float Ds[W][32][T + 1];
     __shared__ float Rho[W][32];
@@ -175,9 +178,9 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
     const float4 Xt = geom[t];
     const int lt = level[t];
     const float inv_st = ldexpf(1.0f, lt);
-    float acc[T];
+    float acc[NO];
 #pragma unroll
-    for (int i = 0; i < T; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < NO; ++i) acc[i] = 0.0f;
     const int b = off[t], e = off[t + 1];
     for (int k0 = b; k0 < e; k0 += 32) {
         const int k = k0 + lane;
@@ -205,6 +208,8 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
 #pragma unroll
                     for (int kb = nk - ka; kb >= 0; --kb) {
                         const int kc = nk - ka - kb;
+                        // the outputs of this slice that k reaches: degrees 0 .. P-1-nk
+                        if (N0 >= MI<P>::idx(P - nk, 0, 0)) continue;
                         const float m = Mj[MI<P>::idx(ka, kb, kc) * kB] * rp;
 #pragma unroll
                         for (int nn = 0; nn + nk < P; ++nn)
@@ -213,8 +218,9 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
 #pragma unroll
                                 for (int nb = nn - na; nb >= 0; --nb) {
                                     const int nc = nn - na - nb;
-                                    acc[MI<P>::idx(na, nb, nc)] =
-                                        fmaf(m, D[MI<P>::idx(na + ka, nb + kb, nc + kc)], acc[MI<P>::idx(na, nb, nc)]);
+                                    const int in = MI<P>::idx(na, nb, nc);
+                                    if (in >= N0 && in < N1)
+                                        acc[in - N0] = fmaf(m, D[MI<P>::idx(na + ka, nb + kb, nc + kc)], acc[in - N0]);
                                 }
                     }
                 rp *= rho;
@@ -224,7 +230,10 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
     }
     float *dst = Lb + (size_t)t * TP * kB + lane;
 #pragma unroll
-    for (int i = 0; i < TP; ++i) dst[i * kB] = i < T ? acc[i] * inv_st : 0.0f;
+    for (int i = 0; i < NO; ++i) dst[(N0 + i) * kB] = acc[i] * inv_st;
+    if (N1 == T)
+#pragma unroll
+        for (int i = T; i < TP; ++i) dst[i * kB] = 0.0f;
 }
 
 template <int P>
@@ -637,8 +646,18 @@ template <int P> static int batch_impl(Handle &h, const float *q, int nrhs, floa
     phase_end(h, FMM_PHASE_UPWARD);
     phase_begin(h, FMM_PHASE_M2L);
     ++h.launches;
-    k_m2l_batch<P><<<ceil_div((int64_t)nc * 32, kM2LBatchThreads), kM2LBatchThreads, 0, h.stream>>>(
-        nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
+    {
+        constexpr int T = MI<P>::T;
+        constexpr int H = P >= 8 ? ((T / 2 + 3) & ~3) : T;   // two launches at P = 8
+        const int mb = ceil_div((int64_t)nc * 32, kM2LBatchThreads);
+        k_m2l_batch<P, 0, H><<<mb, kM2LBatchThreads, 0, h.stream>>>(
+            nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
+        if constexpr (H < T) {
+            ++h.launches;
+            k_m2l_batch<P, H, T><<<mb, kM2LBatchThreads, 0, h.stream>>>(
+                nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
+        }
+    }
     phase_end(h, FMM_PHASE_M2L);
     phase_begin(h, FMM_PHASE_DOWNWARD);
     for (int l = 1; l < h.nlevels; ++l) {
