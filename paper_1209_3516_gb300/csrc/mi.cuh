@@ -88,31 +88,6 @@ __device__ __forceinline__ void laplace_derivatives(float Rx, float Ry, float Rz
     }
 }
 
-// acc[idx(n)] += sum_{|k| <= P-1-|n|} Mk[idx(k)] * D[idx(n+k)]   (the M2L contraction).
-template <int P>
-__device__ __forceinline__ void m2l_contract(const float *Mk, const float *D, float *acc)
-{
-#pragma unroll
-    for (int nk = 0; nk < P; ++nk)
-#pragma unroll
-        for (int ka = nk; ka >= 0; --ka)
-#pragma unroll
-            for (int kb = nk - ka; kb >= 0; --kb) {
-                const int kc = nk - ka - kb;
-                const float m = Mk[MI<P>::idx(ka, kb, kc)];
-#pragma unroll
-                for (int nn = 0; nn + nk < P; ++nn)
-#pragma unroll
-                    for (int na = nn; na >= 0; --na)
-#pragma unroll
-                        for (int nb = nn - na; nb >= 0; --nb) {
-                            const int nc = nn - na - nb;
-                            acc[MI<P>::idx(na, nb, nc)] =
-                                fmaf(m, D[MI<P>::idx(na + ka, nb + kb, nc + kc)], acc[MI<P>::idx(na, nb, nc)]);
-                        }
-            }
-}
-
 // acc[idx(n) - N0] += sum_{|k| <= P-1-|n|} rho^|k| M[idx(k)] D[idx(n+k)] for the
 // outputs with N0 <= idx(n) < N1; M is read from global memory (float4-aligned,
 // TP floats) while the contraction runs, so only D and the accumulators of
