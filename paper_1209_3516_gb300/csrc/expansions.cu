@@ -167,65 +167,64 @@ __device__ __forceinline__ void mi_decode(int i, int &a, int &b, int &c)
 //   Mb_k(P) = 2^-|k| sum_{m <= k} Mb_m(C) prod_i (-s_i)^(k_i - m_i) / (k_i - m_i)!,
 // i.e. three one-dimensional shifts (along x, then y, then z), each
 //   A_k = sum_{j = 0..k_i} B_{k - j e_i} (-s_i)^j / j!,
-// which read only lower indices of the same truncated set.  One warp per
+// which read only lower indices of the same truncated set.  One block per
 // parent cell; all of its children are shifted at once: the work items of a
-// pass are the (child, coefficient) pairs, spread over the lanes, with the
-// children's coefficients, the decoded multi-indices and the per-axis factors
-// in shared memory (no division, no dependence between children).
-constexpr int kM2MWarps = 4;
+// pass are the (child, coefficient) pairs, spread over the block's threads,
+// with the children's coefficients, the decoded multi-indices and the per-axis
+// factors in shared memory (no division, no dependence between children).  A
+// block rather than a warp per parent: the upper levels hold a handful of
+// parents, and one warp walking its ~3 x 30 work items per pass serially took
+// ~40 us per level whatever the level's size.
+constexpr int kM2MThreads = 128;
 
 template <int P>
-__global__ void __launch_bounds__(kM2MWarps * 32) k_m2m_sep(int lo, int n, const int *cbeg, const int *ccnt,
-                                                              const float4 *geom, float *M)
+__global__ void __launch_bounds__(kM2MThreads) k_m2m_sep(int lo, const int *cbeg, const int *ccnt,
+                                                         const float4 *geom, float *M)
 {
     constexpr int T = MI<P>::T, TP = MI<P>::TP;
-    __shared__ float buf_s[kM2MWarps][2][8][T];
-    __shared__ float fac_s[kM2MWarps][8][3][P];   // (-s_i)^j / j! per child and axis
-    __shared__ unsigned char abc_s[T][4];          // multi-index (a, b, c, |k|) of each storage index
-    const int w = threadIdx.x >> 5;
-    const int lane = (int)lane_id();
-    for (int k = threadIdx.x; k < T; k += blockDim.x) {
-        int a, b, c;
-        mi_decode(k, a, b, c);
+    __shared__ float buf_s[2][8][T];
+    __shared__ float fac_s[8][3][P];   // (-s_i)^j / j! per child and axis
+    __shared__ unsigned char abc_s[T][4];   // multi-index (a, b, c, |k|) of each storage index
+    const int c = lo + (int)blockIdx.x;
+    const int nch = ccnt[c];
+    if (nch == 0) return;   // leaf (the whole block): its multipole comes from P2M
+    const int tid = (int)threadIdx.x;
+    for (int k = tid; k < T; k += kM2MThreads) {
+        int a, b, cc;
+        mi_decode(k, a, b, cc);
         abc_s[k][0] = (unsigned char)a;
         abc_s[k][1] = (unsigned char)b;
-        abc_s[k][2] = (unsigned char)c;
-        abc_s[k][3] = (unsigned char)(a + b + c);
+        abc_s[k][2] = (unsigned char)cc;
+        abc_s[k][3] = (unsigned char)(a + b + cc);
     }
-    __syncthreads();
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    const int c = lo + i;
-    const int nch = ccnt[c];
-    if (nch == 0) return;   // leaf: its multipole comes from P2M
     const int cb = cbeg[c];
     const float4 Xp = geom[c];
-    float(*A)[T] = buf_s[w][0];
-    float(*B)[T] = buf_s[w][1];
-    for (int e = lane; e < nch * 3 * P; e += 32) {
+    float(*A)[T] = buf_s[0];
+    float(*B)[T] = buf_s[1];
+    for (int e = tid; e < nch * 3 * P; e += kM2MThreads) {
         const int ch = e / (3 * P), ax = (e / P) % 3, j = e % P;
         const float4 Xc = geom[cb + ch];
         const float pc = ax == 0 ? Xc.x : (ax == 1 ? Xc.y : Xc.z), pp = ax == 0 ? Xp.x : (ax == 1 ? Xp.y : Xp.z);
         float f = 1.0f;
         const float sgn = pc > pp ? -1.0f : 1.0f;
         for (int d = 1; d <= j; ++d) f *= sgn * (1.0f / (float)d);   // constant per call: d <= 7
-        fac_s[w][ch][ax][j] = f;
+        fac_s[ch][ax][j] = f;
     }
-    for (int e = lane; e < nch * T; e += 32) {
+    for (int e = tid; e < nch * T; e += kM2MThreads) {
         const int ch = e / T, k = e % T;
         A[ch][k] = M[(size_t)(cb + ch) * TP + k];
     }
-    __syncwarp();
+    __syncthreads();
     // three passes: x (A -> B), y (B -> A), z (A -> B)
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         float(*src)[T] = (ax == 1) ? B : A;
         float(*dst)[T] = (ax == 1) ? A : B;
-        for (int e = lane; e < nch * T; e += 32) {
+        for (int e = tid; e < nch * T; e += kM2MThreads) {
             const int ch = e / T, k = e % T;
             const int ka = abc_s[k][0], kb = abc_s[k][1], kc = abc_s[k][2];
             const int kx = ax == 0 ? ka : (ax == 1 ? kb : kc);
-            const float *f = fac_s[w][ch][ax];
+            const float *f = fac_s[ch][ax];
             float t = 0.0f;
 #pragma unroll
             for (int d = 0; d < P; ++d) {
@@ -235,11 +234,11 @@ __global__ void __launch_bounds__(kM2MWarps * 32) k_m2m_sep(int lo, int n, const
             }
             dst[ch][k] = t;
         }
-        __syncwarp();
+        __syncthreads();
     }
     // sum over the children, scale by 2^-|k|
     float *out = M + (size_t)c * TP;
-    for (int k = lane; k < TP; k += 32) {
+    for (int k = tid; k < TP; k += kM2MThreads) {
         float s = 0.0f;
         if (k < T) {
             for (int ch = 0; ch < nch; ++ch) s += B[ch][k];
@@ -368,9 +367,10 @@ template <int P> static int m2m_levels(Handle &h, float *M)
 {
     for (int l = h.nlevels - 2; l >= 0; --l) {
         const int lo = (int)h.level_off[l], n = (int)(h.level_off[l + 1] - h.level_off[l]);
+        if (n <= 0) continue;
         ++h.launches;
-        k_m2m_sep<P><<<ceil_div((int64_t)n * 32, kM2MWarps * 32), kM2MWarps * 32, 0, h.stream>>>(
-            lo, n, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(), h.c_geom.as<float4>(), M);
+        k_m2m_sep<P><<<n, kM2MThreads, 0, h.stream>>>(lo, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
+                                                       h.c_geom.as<float4>(), M);
     }
     FMM_CHECK_LAUNCH("upward pass");
     return FMM_OK;
