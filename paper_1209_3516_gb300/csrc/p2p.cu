@@ -42,13 +42,13 @@ namespace fmm {
 #endif
 constexpr int kP2PG = FMM_P2P_G;   // targets per work item (multiple of 4, at most 16)
 constexpr int kP2PGKahan = 8;      // targets per work item with compensated accumulation
-constexpr int kP2PThreads = 128;
+constexpr int kP2PThreads = 64;   // two warps per block: a block's slot is freed as soon as its two items end
 
 #ifndef FMM_P2P_SLOTS
 #define FMM_P2P_SLOTS 256
 #endif
 #ifndef FMM_P2P_MIN_BLOCKS
-#define FMM_P2P_MIN_BLOCKS 3
+#define FMM_P2P_MIN_BLOCKS 6
 #endif
 #ifndef FMM_P2P_UNROLL
 #define FMM_P2P_UNROLL 1
@@ -181,27 +181,55 @@ __device__ __forceinline__ void p2p_tile(const float4 &s, const float2 *ntx, con
                                          float2 *acc)
 {
     constexpr float kEps = 1.17549435e-38f;
+    constexpr int HG = 2;   // target pairs whose chains are written side by side (each step of both, then the next)
     const float2 sx = make_float2(s.x, s.x), sy = make_float2(s.y, s.y), sz = make_float2(s.z, s.z);
     const float2 sq = make_float2(s.w, s.w);
     const float2 eps = make_float2(kEps, kEps);
 #pragma unroll
-    for (int h = 0; h < NT / 2; ++h) {
-        const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps)));
-        float2 rinv;
-        if (kExact) {
-            rinv.x = r2.x > kEps ? rsqrt_approx(r2.x) : 0.0f;
-            rinv.y = r2.y > kEps ? rsqrt_approx(r2.y) : 0.0f;
-        } else {
-            rinv.x = rsqrt_approx(r2.x);
-            rinv.y = rsqrt_approx(r2.y);
-        }
-        const float2 qr = __fmul2_rn(sq, rinv);
-        const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(rinv, rinv));
-        acc[4 * h + 0] = __fadd2_rn(acc[4 * h + 0], qr);
-        acc[4 * h + 1] = __ffma2_rn(qr3, dx, acc[4 * h + 1]);
-        acc[4 * h + 2] = __ffma2_rn(qr3, dy, acc[4 * h + 2]);
-        acc[4 * h + 3] = __ffma2_rn(qr3, dz, acc[4 * h + 3]);
+    for (int h0 = 0; h0 < NT / 2; h0 += HG) {
+        float2 dx[HG], dy[HG], dz[HG], r2[HG], rinv[HG], qr[HG], qr3[HG];
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) {
+                dx[j] = __fadd2_rn(sx, ntx[h0 + j]);
+                dy[j] = __fadd2_rn(sy, nty[h0 + j]);
+                dz[j] = __fadd2_rn(sz, ntz[h0 + j]);
+            }
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) r2[j] = __ffma2_rn(dx[j], dx[j], eps);
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) r2[j] = __ffma2_rn(dy[j], dy[j], r2[j]);
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) r2[j] = __ffma2_rn(dz[j], dz[j], r2[j]);
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) {
+                if (kExact) {
+                    rinv[j].x = r2[j].x > kEps ? rsqrt_approx(r2[j].x) : 0.0f;
+                    rinv[j].y = r2[j].y > kEps ? rsqrt_approx(r2[j].y) : 0.0f;
+                } else {
+                    rinv[j].x = rsqrt_approx(r2[j].x);
+                    rinv[j].y = rsqrt_approx(r2[j].y);
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) {
+                qr[j] = __fmul2_rn(sq, rinv[j]);
+                qr3[j] = __fmul2_rn(qr[j], __fmul2_rn(rinv[j], rinv[j]));
+            }
+#pragma unroll
+        for (int j = 0; j < HG; ++j)
+            if (h0 + j < NT / 2) {
+                const int h = h0 + j;
+                acc[4 * h + 0] = __fadd2_rn(acc[4 * h + 0], qr[j]);
+                acc[4 * h + 1] = __ffma2_rn(qr3[j], dx[j], acc[4 * h + 1]);
+                acc[4 * h + 2] = __ffma2_rn(qr3[j], dy[j], acc[4 * h + 2]);
+                acc[4 * h + 3] = __ffma2_rn(qr3[j], dz[j], acc[4 * h + 3]);
+            }
     }
 }
 
@@ -334,7 +362,6 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
 
     RunCursor cur;
     cur.init(roff, it.w, run, run_end);
-    // the item computes ceil(tc / 4) * 4 targets (extra ones repeat the last target)
     // the item computes tc rounded up to 4 (tc <= 8) or to 2 (tc > 8) targets, extra
     // ones repeating the last target: balanced slices of leaves of 13-55
     // particles hold 9-16 targets, where rounding to 4 would add ~9 % of pairs
