@@ -60,3 +60,28 @@ def test_reference_arm_off_rank_zero_does_no_work(monkeypatch):
     a = types.SimpleNamespace(N=10, P=4, theta=0.4, ncrit=64, steps=1, warmup=0, gpus=2, dist="uniform",
                               kahan=False)
     assert bench.run_reference(a) == 0
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm (the oracle on the host cores) prints the benchmark's
+    JSON line: the same metric and workload keys as the GPU arm, impl, a
+    cpu_baseline describing the run and an e2e with no device copies."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "16384",
+                        "--P", "4", "--theta", "0.4", "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["unit"] == "evals/s"
+    assert d["config"]["N"] == 16384 and "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["e2e"]["d2h_bytes_per_step"] == 0
