@@ -77,7 +77,6 @@ void phase_end(Handle &h, int phase)
     if (h.events_ready && (h.flags & FMM_FLAG_TIMING)) cudaEventRecord(h.ev[2 * phase + 1], h.stream);
 }
 
-static bool supported_order(int P) { return P == 3 || P == 4 || P == 5 || P == 6 || P == 8; }
 
 // Pins the handle's device for the duration of a call and restores the caller's.
 struct DeviceGuard {

@@ -62,6 +62,9 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Expansion orders compiled into the library.
+inline bool supported_order(int P) { return P == 3 || P == 4 || P == 5 || P == 6 || P == 8; }
+
 // Device-side counters of the traversal (one struct, zeroed per traversal).
 struct TravCounters {
     unsigned long long n_m2l;     // pairs emitted to the M2L list

@@ -331,6 +331,15 @@ int fmm_multi_create(fmm_multi **mp, int nsys, const int64_t *N, int P, float th
         set_error("fmm_multi_create: total N must be below 2^31");
         return FMM_ERR_ARG;
     }
+    // the per-system checks of fmm_create, before any device call
+    if (!(theta >= 0.0f && theta < 1.0f) || ncrit < 1) {
+        set_error("fmm_multi_create: theta must be in [0, 1) and ncrit >= 1");
+        return FMM_ERR_ARG;
+    }
+    if (!supported_order(P)) {
+        set_error("fmm_multi_create: expansion order P must be one of 3, 4, 5, 6, 8");
+        return FMM_ERR_UNSUPPORTED;
+    }
     fmm_multi *w = new (std::nothrow) fmm_multi;
     if (!w) {
         set_error("fmm_multi_create: out of host memory");

@@ -82,3 +82,58 @@ def test_backward_argument_checks(lib):
     lib.fmm_last_error_string.restype = ctypes.c_char_p
     assert lib.fmm_backward(None, None, None, None, None) == -1
     assert b"null handle" in lib.fmm_last_error_string()
+
+
+def test_every_entry_point_rejects_null_arguments_before_any_device_call(lib):
+    """A null handle or output pointer is an FMM_ERR_ARG (-1) with a message,
+    from every entry point, without touching the device."""
+    V = ctypes.c_void_p
+    lib.fmm_last_error_string.restype = ctypes.c_char_p
+    calls = [
+        ("fmm_evaluate", (V(), V(), V(), V(), V())),
+        ("fmm_evaluate_host", (V(), V(), V(), V(), V())),
+        ("fmm_evaluate_batch", (V(), V(), V(), ctypes.c_int(4), V(), V())),
+        ("fmm_energy", (V(), V())),
+        ("fmm_energy_noalloc", (V(), V(), ctypes.c_int64(10), V(), V())),
+        ("fmm_stats", (V(), V())),
+        ("fmm_set_hybrid", (V(), ctypes.c_int64(0))),
+        ("fmm_get_norm", (V(), V(), V())),
+        ("fmm_get_sorted", (V(), V(), V())),
+        ("fmm_get_ncells", (V(), V())),
+        ("fmm_get_lists", (V(), V(), V(), V(), V())),
+        ("fmm_get_cells", (V(),) + (V(),) * 8),
+        ("fmm_multi_build", (V(), V())),
+        ("fmm_multi_evaluate", (V(), V(), V(), V())),
+        ("fmm_multi_info", (V(), V())),
+        ("fmm_multi_set_hybrid", (V(), ctypes.c_int64(0))),
+    ]
+    for name, args in calls:
+        assert getattr(lib, name)(*args) == -1, name
+        assert lib.fmm_last_error_string().startswith(name.encode()), name
+    assert lib.fmm_multi_destroy(V()) == 0
+
+
+def test_multi_and_tuner_argument_checks(lib):
+    V = ctypes.c_void_p
+    lib.fmm_last_error_string.restype = ctypes.c_char_p
+    h = V()
+    sizes = (ctypes.c_int64 * 2)(100, 200)
+    create = lambda *a: lib.fmm_multi_create(*a)
+    f4 = ctypes.c_float
+    assert create(ctypes.byref(h), ctypes.c_int(0), sizes, 4, f4(0.4), 64, V()) == -1     # no systems
+    assert create(ctypes.byref(h), ctypes.c_int(2), V(), 4, f4(0.4), 64, V()) == -1       # no sizes
+    assert create(V(), ctypes.c_int(2), sizes, 4, f4(0.4), 64, V()) == -1                # no handle pointer
+    bad = (ctypes.c_int64 * 2)(100, 0)
+    assert create(ctypes.byref(h), ctypes.c_int(2), bad, 4, f4(0.4), 64, V()) == -1      # an empty system
+    assert create(ctypes.byref(h), ctypes.c_int(2), sizes, 4, f4(1.0), 64, V()) == -1    # theta out of range
+    assert create(ctypes.byref(h), ctypes.c_int(2), sizes, 4, f4(0.4), 0, V()) == -1     # ncrit < 1
+    assert create(ctypes.byref(h), ctypes.c_int(2), sizes, 7, f4(0.4), 64, V()) == -2    # P not compiled
+    assert b"P must be" in lib.fmm_last_error_string()
+    best64, best32 = ctypes.c_int64(), ctypes.c_int()
+    ms = (ctypes.c_double * 4)()
+    cand = (ctypes.c_int64 * 2)(0, 256)
+    assert lib.fmm_tune_hybrid(ctypes.c_int64(0), 4, f4(0.4), 64, V(), V(), cand, 2, 1, V(), ctypes.byref(best64),
+                               ms) == -1
+    ci = (ctypes.c_int * 2)(32, 64)
+    assert lib.fmm_tune_ncrit(ctypes.c_int64(0), 4, f4(0.4), V(), V(), ci, 2, 1, V(), ctypes.byref(best32),
+                              ms) == -1
