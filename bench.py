@@ -28,6 +28,7 @@ import subprocess
 import sys
 import threading
 import time
+from math import comb
 
 import numpy as np
 
@@ -37,6 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FMM evals/s & P2P Gpair/s at N=1M, rel err 1e-4, vs plain FP32 path"
 FLOPS_PER_PAIR = 20          # the paper's count for a potential + force interaction (Table 4)
 FP32_LANES_PER_SM = 128
+P2P_FP32_OPS_PER_PAIR = 13   # 3 sub, 3 FMA (r^2), 3 mul, 1 add, 3 FMA: the P2P kernel's FP32 work per pair
 
 
 def parse():
@@ -62,6 +64,7 @@ def parse():
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
+    ap.add_argument("--peaks-only", action="store_true", help="measure the FP32 / SFU peaks only and print them")
     ap.add_argument("--batch-n", type=int, default=1048576, help="N of the batched variant (a smaller case for ncu)")
     return ap.parse_args()
 
@@ -88,42 +91,45 @@ def config(a):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(a, x, q):
-    """Uniform cube: the particles in the octant [0, 1/2)^3 (same density, same
-    leaves).  Plummer: the first N/16 particles (a Plummer sphere of N/16)."""
-    if a.dist == "plummer":
-        n = max(1, a.N // 16)
-        return x[:n], q[:n]
-    m = np.all(x < 0.5, axis=1)
-    return x[m], q[m]
+def error_sample(N):
+    """The 4,096-target error sample: every (N // 4096)-th target of the original order."""
+    step = max(1, N // 4096)
+    return np.arange(0, N, step, dtype=np.int64)[:4096]
 
 
-def sample_words(a, n):
-    if a.dist == "plummer":
-        return "the first %d particles of the workload (a Plummer sphere of that size)" % n
-    return "the %d particles of the workload in the octant [0,1/2)^3 (same density and leaves)" % n
-
-
-def time_oracle(a, xs, qs, reps=1):
+def time_oracle(a, x, q, reps=1):
+    """Seconds of the FP64 oracle FMM (build + evaluate) on the whole workload, per repetition."""
     import oracle
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        f = oracle.FMM(xs.shape[0], a.P, a.theta, a.ncrit).build(xs)
-        f.evaluate(qs)
+        f = oracle.FMM(x.shape[0], a.P, a.theta, a.ncrit).build(x)
+        f.evaluate(q)
         ts.append(time.perf_counter() - t0)
     return ts
 
 
-def cpu_baseline(a, x, q, reps=1):
+def cpu_baseline(a, x, q, reps=3):
+    """The oracle on the host cores at the full workload (no sampling or scaling):
+    the FP64 FMM, median of `reps` build + evaluate runs, and the FP64 direct sum
+    on the 4,096-target error sample."""
     import oracle
-    xs, qs = oracle_sample(a, x, q)
-    ts = time_oracle(a, xs, qs, reps)
-    t_full = statistics.median(ts) * a.N / xs.shape[0]
-    return {"value": 1.0 / t_full, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "FP64 oracle FMM (build + evaluate, same P/theta/ncrit) on %s, time scaled by N/%d"
-                      % (sample_words(a, xs.shape[0]), xs.shape[0]),
-            "seconds_per_sample": statistics.median(ts)}
+    q64 = q.astype(np.float32).astype(np.float64)
+    ts = time_oracle(a, x, q64, reps)
+    tgt = error_sample(a.N)
+    t0 = time.perf_counter()
+    ref = oracle.direct(x, q64, targets=tgt)
+    t_direct = time.perf_counter() - t0
+    cpu_baseline.last_direct = (tgt, ref)
+    return {"value": 1.0 / statistics.median(ts), "unit": "evals/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "the whole workload (N=%d): FP64 oracle FMM, build + evaluate, same P/theta/ncrit, "
+                      "median of %d runs" % (a.N, reps),
+            "seconds_per_eval": statistics.median(ts), "seconds_all": ts,
+            "direct_sum_sample": {"targets": int(tgt.shape[0]), "sources": a.N, "seconds": t_direct,
+                                  "pairs_per_s": tgt.shape[0] * a.N / t_direct,
+                                  "what": "FP64 direct sum (potential + gradient) on the 4,096-target "
+                                          "error sample against all N sources"}}
 
 
 def p2p_traffic(a):
@@ -256,25 +262,27 @@ def max_over_ranks(pg, v):
 # arms
 # ---------------------------------------------------------------------------
 def run_reference(a):
+    """The reference arm: the CPU oracle (FP64 C, OpenMP, all host cores), each
+    step one build + evaluate of the FP64 FMM on the whole workload."""
     # under torchrun only rank 0 times the oracle; the other ranks exit without work
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     import oracle
     x, q = workload(a)
-    xs, qs = oracle_sample(a, x, q)
-    time_oracle(a, xs, qs, reps=max(0, a.warmup))
+    q64 = q.astype(np.float32).astype(np.float64)
+    time_oracle(a, x, q64, reps=max(0, a.warmup))
     t0 = time.perf_counter()
-    ts = time_oracle(a, xs, qs, reps=a.steps)
+    ts = time_oracle(a, x, q64, reps=a.steps)
     wall = time.perf_counter() - t0
-    scale = a.N / xs.shape[0]
-    per_eval = statistics.mean(ts) * scale
+    per_eval = sum(ts) / len(ts)
     value = 1.0 / per_eval
+    sample = ("each step: the whole workload (N=%d), FP64 oracle FMM, build + evaluate, same P/theta/ncrit"
+              % a.N)
     line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "evals/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(a),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": "each step: FP64 oracle FMM (build + evaluate) on %s, time scaled by N/%d"
-                                       % (sample_words(a, xs.shape[0]), xs.shape[0])},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line))
@@ -574,9 +582,21 @@ def run_ours(a):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    nominal_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = pairs * FLOPS_PER_PAIR / (p2p_mean * 1e-3) / 1e12
     traffic = p2p_traffic(a)
+    # the FP32 FMA and SFU rates of this GPU, measured now (fmm_measure_peaks)
+    # with the clocks sampled while they run
+    pk_sampler = ClockSampler(gpu_id_for_smi(dev))
+    pk_sampler.start()
+    time.sleep(0.2)
+    peaks = fmm.measure_peaks(stream)
+    pk_clocks = pk_sampler.stop()
+    peak_tflops = max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
+    pair_rate = pairs / (p2p_mean * 1e-3)
+    # M2L: the truncated contraction's flops per cell pair (2 C(P+5, 6)), both launches
+    m2l_mean = statistics.mean(m2l_ms)
+    m2l_flops = 2 * comb(a.P + 5, 6) * st["n_m2l"]
 
     # fmm_evaluate alone on the built tree (the paper's
     # "FMM evals/s": tree construction excluded); reported beside the build +
@@ -613,7 +633,24 @@ def run_ours(a):
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                              "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
                              "launch_ms": p2p_mean,
-                             "peak_basis": "%d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % (sms, sm_max)},
+                             "peak_basis": "measured on this GPU in this run: fmm_measure_peaks (register-only "
+                                           "FFMA / FFMA2 chains over every SM, fastest of 5 launches, CUDA "
+                                           "events), FP32 FMA peak = the faster of the two; nominal %d SMs x 128 "
+                                           "lanes x 2 x %.0f MHz = %.1f TFLOP/s" % (sms, sm_max, nominal_tflops),
+                             "measured_peaks": dict(peaks, clocks=pk_clocks),
+                             "fp32_pipe_frac": pair_rate * P2P_FP32_OPS_PER_PAIR / (peak_tflops * 1e12 / 2),
+                             "sfu_frac": pair_rate / peaks["rsqrt_per_s"],
+                             "pipe_note": "fp32_pipe_frac: %d FP32 operations per pair (3 sub, 3 FMA for r^2, 3 mul, "
+                                          "1 add, 3 FMA) against the measured FMA operation rate; sfu_frac: one "
+                                          "rsqrt per pair against the measured SFU rsqrt rate"
+                                          % P2P_FP32_OPS_PER_PAIR},
+                "m2l_roofline": {"kernel": "k_m2l", "bound": "alu", "unit": "TFLOP/s",
+                                 "achieved": m2l_flops / (m2l_mean * 1e-3) / 1e12, "peak": peak_tflops,
+                                 "frac": m2l_flops / (m2l_mean * 1e-3) / 1e12 / peak_tflops,
+                                 "flops_per_pair": 2 * comb(a.P + 5, 6), "pairs_per_launch": st["n_m2l"],
+                                 "launch_ms": m2l_mean,
+                                 "flops_note": "truncated contraction |n|+|k|<=P-1 only (2 C(P+5,6) per cell "
+                                               "pair); the per-pair derivative recurrence is not counted"},
                 "evaluate_only": {"evals_per_s": 1e3 / ms_eval_only, "ms": ms_eval_only,
                                   "particles_per_s": a.N * 1e3 / ms_eval_only},
                 "phases_ms": {k: statistics.mean(v) for k, v in phase_acc.items()},
@@ -624,6 +661,17 @@ def run_ours(a):
                 "clocks": clocks}
         if not a.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(a, x, q)
+            # accuracy of this run's result against the FP64 direct sum on the error sample
+            tgt, (pr, gr) = cpu_baseline.last_direct
+            h.evaluate(qd, phi=phi, grad=grad)
+            torch.cuda.synchronize()
+            pg = phi.cpu().numpy().astype(np.float64)[tgt]
+            gg = grad.cpu().numpy().astype(np.float64)[tgt]
+            line["accuracy"] = {"phi_rel_l2_vs_direct": float(np.linalg.norm(pg - pr) / np.linalg.norm(pr)),
+                                "grad_rel_l2_vs_direct": float(np.linalg.norm(gg - gr) / np.linalg.norm(gr)),
+                                "sample": "%d targets (every %d-th of the original order), FP64 direct sum over "
+                                          "all N sources" % (tgt.shape[0], max(1, a.N // 4096)),
+                                "bar": 1e-4}
     h.close()
     if line is not None and a.variants != "none" and ws == 1 and a.dist == "uniform":
         try:
@@ -638,8 +686,27 @@ def run_ours(a):
     return 0
 
 
+def run_peaks():
+    """The FP32 FMA / FFMA2 and SFU rsqrt rates of GPU 0 with the clocks sampled meanwhile."""
+    import torch
+    from paper_1209_3516_gb300 import fmm
+    torch.cuda.set_device(0)
+    smp = ClockSampler(gpu_id_for_smi(0))
+    smp.start()
+    time.sleep(0.3)
+    pk = fmm.measure_peaks()
+    clocks = smp.stop()
+    props = torch.cuda.get_device_properties(0)
+    print(json.dumps(dict(pk, clocks=clocks, gpu=props.name,
+                          how="fmm_measure_peaks: register-only FFMA, FFMA2 and rsqrt.approx chains, one full "
+                              "wave on every SM, fastest of 5 launches timed with CUDA events")))
+    return 0
+
+
 def main():
     a = parse()
+    if a.peaks_only:
+        return run_peaks()
     if a.impl == "reference":
         return run_reference(a)
     if a.variants_only:

@@ -191,6 +191,27 @@ int fmm_energy(fmm_handle *h, double *E);
 int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq, float *dx);
 
 /*
+ * fmm_measure_peaks -- the FP32 roofline denominators of the current GPU,
+ * measured (the paper has no counterpart; it quotes its CPU's data-sheet
+ * peak).  Three register-only kernels run one full wave on every SM: scalar
+ * FFMA chains, packed FFMA2 chains and rsqrt.approx (SFU) chains; each is
+ * launched 5 times on `stream` (NULL = legacy default stream) and the fastest
+ * launch, timed with CUDA events, is kept.  Blocks until done (~0.3 s).
+ * Allocates a small sink buffer (one float per resident thread) with
+ * cudaMallocAsync on the stream.  FMA counts as 2 flops.
+ *   out  HOST pointer, filled on success.
+ */
+typedef struct fmm_peaks {
+    double ffma_tflops;     /* scalar FFMA, TFLOP/s */
+    double ffma2_tflops;    /* packed FFMA2, TFLOP/s */
+    double rsqrt_per_s;     /* SFU rsqrt.approx operations per second */
+    double ms_ffma, ms_ffma2, ms_rsqrt;   /* fastest launch of each kernel */
+    int32_t sms;
+    int32_t reserved;
+} fmm_peaks;
+int fmm_measure_peaks(fmm_peaks *out, void *stream);
+
+/*
  * fmm_energy_noalloc -- E = 1/2 sum_i q_i phi_i of caller arrays, reduced in FP64,
  * WITHOUT allocating any memory.  The paper has no counterpart: this entry point
  * exists for callers that cannot let a library call cudaMalloc, such as
@@ -203,11 +224,16 @@ int fmm_backward(fmm_handle *h, const float *dphi, const float *dgrad, float *dq
  *           library holds until the process exits.
  *   E       out, DEVICE pointer to one double.
  *   stream  cudaStream_t to run on (NULL = legacy default stream); asynchronous.
+ * q, phi and E must be device memory of the current GPU (or managed memory):
+ * each pointer's kind is checked with cudaPointerGetAttributes before any
+ * launch, and a host pointer (such as the host double that fmm_energy takes)
+ * or another GPU's memory returns FMM_ERR_ARG.
  * The first call on a device (with that device current) looks up the scratch
- * array's device address; make that first call before any stream capture.  All
- * calls share the scratch array, so calls that overlap on the GPU (different
- * streams or threads) race; the array keeps the last call's contents, and each
- * call writes every partial it reads.
+ * array's device address and caches it with the current CUDA context (a new
+ * context, e.g. after a device reset, is looked up again); make that first
+ * call before any stream capture.  All calls share the scratch array, so calls
+ * that overlap on the GPU (different streams or threads) race; the array keeps
+ * the last call's contents, and each call writes every partial it reads.
  */
 int fmm_energy_noalloc(const float *q, const float *phi, int64_t n, double *E, void *stream);
 

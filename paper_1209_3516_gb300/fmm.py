@@ -48,6 +48,12 @@ class _Stats(ctypes.Structure):
 MAX_RHS = 32
 
 
+class _Peaks(ctypes.Structure):
+    _fields_ = [("ffma_tflops", ctypes.c_double), ("ffma2_tflops", ctypes.c_double), ("rsqrt_per_s", ctypes.c_double),
+                ("ms_ffma", ctypes.c_double), ("ms_ffma2", ctypes.c_double), ("ms_rsqrt", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class _MultiInfo(ctypes.Structure):
     _fields_ = [("n_total", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
                 ("n_m2l", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
@@ -91,6 +97,7 @@ def load():
     L.fmm_get_cells.argtypes = [_vp] + [_vp] * 8
     L.fmm_get_lists.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _vp, _vp]
     L.fmm_energy_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+    L.fmm_measure_peaks.argtypes = [ctypes.POINTER(_Peaks), _vp]
     L.fmm_multi_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                    ctypes.c_float, ctypes.c_int, ctypes.POINTER(_Options)]
     L.fmm_multi_build.argtypes = [_vp, _vp]
@@ -163,16 +170,32 @@ def tune_hybrid(x, q, P, theta, ncrit=64, candidates=(-1, 0, 256, 512, 1024, 204
     return best.value, {c: ms[i] for i, c in enumerate(candidates)}
 
 
+def measure_peaks(stream=None):
+    """fmm_measure_peaks on the current device: FP32 FFMA / FFMA2 TFLOP/s and SFU rsqrt/s, measured."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    pk = _Peaks()
+    _check(load().fmm_measure_peaks(ctypes.byref(pk), ctypes.c_void_p(stream.cuda_stream)))
+    return {f: getattr(pk, f) for f, _ in _Peaks._fields_ if f != "reserved"}
+
+
 def energy_noalloc(q, phi, E, stream=None):
-    """fmm_energy_noalloc: E[0] = 1/2 sum q phi into the caller's device double E (no allocation)."""
+    """fmm_energy_noalloc: E[0] = 1/2 sum q phi into the caller's device double E (no allocation).
+
+    q, phi and E must sit on one CUDA device; the call runs with that device current."""
     import torch
     n = q.numel()
-    qp = _dev_ptr(q, torch.float32, (n,), "q")
-    pp = _dev_ptr(phi, torch.float32, (n,), "phi")
-    ep = _dev_ptr(E, torch.float64, (1,), "E")
-    if stream is None:
-        stream = torch.cuda.current_stream(q.device)
-    _check(load().fmm_energy_noalloc(qp, pp, n, ep, ctypes.c_void_p(stream.cuda_stream)))
+    devs = {t.device for t in (q, phi, E)}
+    if len(devs) != 1 or q.device.type != "cuda":
+        raise ValueError("energy_noalloc: q, phi and E must be on one CUDA device (got %s)" % sorted(map(str, devs)))
+    with torch.cuda.device(q.device):
+        qp = _dev_ptr(q, torch.float32, (n,), "q")
+        pp = _dev_ptr(phi, torch.float32, (n,), "phi")
+        ep = _dev_ptr(E, torch.float64, (1,), "E")
+        if stream is None:
+            stream = torch.cuda.current_stream(q.device)
+        _check(load().fmm_energy_noalloc(qp, pp, n, ep, ctypes.c_void_p(stream.cuda_stream)))
     return E
 
 

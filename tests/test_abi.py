@@ -95,6 +95,7 @@ def test_every_entry_point_rejects_null_arguments_before_any_device_call(lib):
         ("fmm_evaluate_batch", (V(), V(), V(), ctypes.c_int(4), V(), V())),
         ("fmm_energy", (V(), V())),
         ("fmm_energy_noalloc", (V(), V(), ctypes.c_int64(10), V(), V())),
+        ("fmm_measure_peaks", (V(), V())),
         ("fmm_stats", (V(), V())),
         ("fmm_set_hybrid", (V(), ctypes.c_int64(0))),
         ("fmm_get_norm", (V(), V(), V())),
