@@ -665,9 +665,9 @@ def run_ours(a):
             tgt, (pr, gr) = cpu_baseline.last_direct
             h.evaluate(qd, phi=phi, grad=grad)
             torch.cuda.synchronize()
-            pg = phi.cpu().numpy().astype(np.float64)[tgt]
+            p_gpu = phi.cpu().numpy().astype(np.float64)[tgt]
             gg = grad.cpu().numpy().astype(np.float64)[tgt]
-            line["accuracy"] = {"phi_rel_l2_vs_direct": float(np.linalg.norm(pg - pr) / np.linalg.norm(pr)),
+            line["accuracy"] = {"phi_rel_l2_vs_direct": float(np.linalg.norm(p_gpu - pr) / np.linalg.norm(pr)),
                                 "grad_rel_l2_vs_direct": float(np.linalg.norm(gg - gr) / np.linalg.norm(gr)),
                                 "sample": "%d targets (every %d-th of the original order), FP64 direct sum over "
                                           "all N sources" % (tgt.shape[0], max(1, a.N // 4096)),

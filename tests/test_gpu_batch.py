@@ -34,13 +34,15 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 def peak_rel(a, b):
-    """Largest per-target error over the rms of the reference (per-target vector
-    norm for gradients): a bound on localised errors that the L2 norm can hide."""
+    """Largest per-target error, each over rms(reference) + |reference at that
+    target| (per-target vector norms for gradients): a bound on localised errors
+    that the L2 norm can hide.  The |reference| term admits the FP32 rounding of
+    a target's own largest terms (a close neighbour), which scales with them."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     d = np.abs(a - b) if a.ndim == 1 else np.linalg.norm(a - b, axis=-1)
     r = np.abs(b) if b.ndim == 1 else np.linalg.norm(b, axis=-1)
-    return float(d.max() / np.sqrt(np.mean(r * r)))
+    return float(np.max(d / (np.sqrt(np.mean(r * r)) + r)))
 
 
 def run_batch(torch, x, Q, P, theta, ncrit):
