@@ -104,6 +104,11 @@ static int check_async_errors(Handle &h)
         set_error("P2P staging: a bulk-copy wait gave up; the last evaluation is incomplete");
         return FMM_ERR_CUDA;
     }
+    if (h.pinned->err & 4u) {
+        FMM_CUDA(cudaMemsetAsync(h.err_flag.p, 0, sizeof(unsigned), h.stream));
+        set_error("batched P2P: a tensor-core completion wait gave up; the last batched evaluation is incomplete");
+        return FMM_ERR_CUDA;
+    }
     return FMM_OK;
 }
 
@@ -226,7 +231,7 @@ int fmm_destroy(fmm_handle *w)
                       &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_poff, &h.p2p_ent, &h.p2p_cnt,
                       &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad,
                       &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb, &h.batch_items,
-                      &h.c_scale};
+                      &h.c_scale, &h.tc_items, &h.lbh, &h.lbl, &h.tc_next};
     for (DevBuf *b : bufs) b->release();
     if (h.events_ready)
         for (auto &ev : h.ev) cudaEventDestroy(ev);

@@ -668,19 +668,8 @@ template <int P> static int batch_impl(Handle &h, const float *q, int nrhs, floa
     }
     phase_end(h, FMM_PHASE_DOWNWARD);
     FMM_CHECK_LAUNCH("batched far field");
-    static bool configured[64] = {};
-    if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
-        FMM_CUDA(cudaFuncSetAttribute(k_p2p_batch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmem));
-        configured[h.device] = true;
-    }
-    const double ih = 1.0 / h.norm_host[3];
     phase_begin(h, FMM_PHASE_P2P);
-    ++h.launches;
-    k_p2p_batch<P><<<ceil_div((int64_t)h.n_batch_items * 32, kBThreads), kBThreads, kBSmem, h.stream>>>(
-        (int)h.n_batch_items, h.batch_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
-        h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.qbh.as<__nv_bfloat16>(), h.qbl.as<__nv_bfloat16>(),
-        h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(), h.c_parent.as<int>(), h.c_geom.as<float4>(), Lb,
-        h.perm.as<int>(), N, nrhs, (float)ih, (float)(ih * ih), phi, grad);
+    FMM_TRY(p2p_batch_tc(h, nrhs, phi, grad));
     phase_end(h, FMM_PHASE_P2P);
     FMM_CHECK_LAUNCH("batched p2p");
     return FMM_OK;

@@ -168,6 +168,12 @@ struct Handle {
     DevBuf batch_items;
     int64_t n_batch_items = 0;
     bool batch_items_ready = false;
+    // the tensor-core P2P + L2P of the batched evaluation: work items of <= 32
+    // targets, the leaves' local expansions split into BF16 hi / lo
+    // [leaf][T][32], and the persistent CTAs' work counter
+    DevBuf tc_items, lbh, lbl, tc_next;
+    int64_t n_tc_items = 0;
+    bool tc_items_ready = false;
 
     DevBuf phi_sorted;    // float[N] potential in sorted order (for the energy)
     DevBuf energy_part;   // double partials
@@ -202,6 +208,7 @@ int build_tree(Handle &h, const double *x);       // cells, geometry, leaf-local
 int build_lists(Handle &h);                       // DTT + grouping
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
 int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items);   // items of <= g targets
+int p2p_batch_tc(Handle &h, int nrhs, float *phi, float *grad);   // batched P2P + L2P, tensor cores
 
 int evaluate_upward(Handle &h, const float *q);   // gather q, P2M, M2M
 int evaluate_m2l(Handle &h, const float *M, float *L);
