@@ -144,12 +144,15 @@ int fmm_evaluate(fmm_handle *h, const double *x, const float *q, float *phi, flo
  *   grad  out, device, nrhs x N x 3 FP32 (vector r at grad + 3 r N), or NULL.
  * The same tree, lists and operators as fmm_evaluate, with every operator a
  * contraction over the vectors: P2M, M2M, M2L and L2L apply each geometric
- * factor to all vectors (FP32); the P2P is a dense product on the tensor cores,
- * Phi = G Q over 16-source tiles, with the kernel matrices G (1/r and e/r^3)
- * generated in FP32 and G and Q each split into BF16 high and low parts (three
- * MMAs, FP32 accumulation: about 2^-16 relative per term); L2P and the scatter
- * are fused.  Asynchronous (the first call after a build synchronises once to
- * size its work items).
+ * factor to all vectors (FP32); the P2P and the L2P are one dense product on
+ * the 5th-generation tensor cores per work item of <= 32 targets: D = G Q + W L
+ * with the kernel matrices G (1/r and e/r^3 of every target-source pair) and
+ * the targets' Taylor monomials W generated in FP32 straight into tensor
+ * memory, Q the charges and L the leaf's local expansions, every operand split
+ * into BF16 high and low parts (three tcgen05.mma per K step, FP32
+ * accumulation in tensor memory: about 2^-16 relative per term); the scatter
+ * to caller order is fused.  Asynchronous (the first call after a build
+ * synchronises once to size its work items).
  */
 int fmm_evaluate_batch(fmm_handle *h, const double *x, const float *q, int nrhs, float *phi, float *grad);
 

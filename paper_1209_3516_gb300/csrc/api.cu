@@ -230,7 +230,7 @@ int fmm_destroy(fmm_handle *w)
                       &h.counters, &h.front[0], &h.front[1], &h.m2l_raw, &h.p2p_raw, &h.lkeys, &h.lkeys_alt,
                       &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_poff, &h.p2p_ent, &h.p2p_cnt,
                       &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad,
-                      &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb, &h.batch_items,
+                      &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb,
                       &h.c_scale, &h.tc_items, &h.lbh, &h.lbl, &h.tc_next};
     for (DevBuf *b : bufs) b->release();
     if (h.events_ready)

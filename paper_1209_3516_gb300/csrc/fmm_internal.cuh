@@ -161,13 +161,9 @@ struct Handle {
     bool adj_items_ready = false;
 
     // many charge vectors (fmm_evaluate_batch): charges [N][32] in sorted order
-    // (FP32 and its BF16 hi / lo split), expansions [ncells][TP][32], work items
-    // of <= 8 targets
+    // (FP32 and its BF16 hi / lo split), expansions [ncells][TP][32]
     DevBuf qb, qbh, qbl;
     DevBuf Mb, Lb;
-    DevBuf batch_items;
-    int64_t n_batch_items = 0;
-    bool batch_items_ready = false;
     // the tensor-core P2P + L2P of the batched evaluation: work items of <= 32
     // targets, the leaves' local expansions split into BF16 hi / lo
     // [leaf][T][32], and the persistent CTAs' work counter

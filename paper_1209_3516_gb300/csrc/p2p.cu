@@ -501,7 +501,6 @@ int build_p2p_items(Handle &h)
     FMM_CHECK_LAUNCH("p2p runs");
     // work items (the adjoint's items are built on first use)
     h.adj_items_ready = false;
-    h.batch_items_ready = false;
     h.tc_items_ready = false;
     h.p2p_g = 0;
     return build_work_items(h, (h.flags & FMM_FLAG_KAHAN) ? kP2PGKahan : kP2PG, h.p2p_items, h.n_items);
