@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="all",
                     choices=["all", "none", "adaptive", "differentiated", "batched", "systems", "ncrit",
-                             "hybrid"],
+                             "hybrid", "mutual"],
                     help="variant workloads timed after the main line (adaptive: Plummer N=4M with and "
                          "without compensated P2P; differentiated: N=262144 forward + fmm_backward)")
     ap.add_argument("--variants-only", action="store_true", help="time only the variants (no main line)")
@@ -322,7 +322,40 @@ def run_variants(torch, stream, flush, which="all", batch_n=1048576):
         out.update(variant_ncrit(torch))
     if which in ("all", "hybrid"):
         out.update(variant_hybrid(torch, stream, flush))
+    if which in ("all", "mutual"):
+        out.update(variant_mutual(torch, stream, flush))
     return out
+
+
+def variant_mutual(torch, stream, flush):
+    """The mutual near field (FMM_FLAG_MUTUAL: each unordered leaf pair once, both
+    directions) against the one-sided P2P on the N = 1M uniform workload (P = 8,
+    theta = 0.5, ncrit = 64), build + evaluate, timed like the main line."""
+    from paper_1209_3516_gb300 import fmm, inputs
+    N, P, theta, ncrit = 1048576, 8, 0.5, 64
+    x, q = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    phi = torch.empty(N, dtype=torch.float32, device="cuda")
+    grad = torch.empty(N, 3, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, mu in (("one_sided", False), ("mutual", True)):
+        h = fmm.FMM(N, P, theta, ncrit, mutual=mu, timing=True)
+
+        def step():
+            h.build(xd)
+            h.evaluate(qd, phi=phi, grad=grad)
+        t = time_steps(torch, stream, step, 20, 3, flush)
+        st = h.stats()
+        out[name] = {"evals_per_s": 1e3 / t, "ms": t, "p2p_ms": st["ms_phase"]["p2p"],
+                     "lists_ms": st["ms_phase"]["lists"], "p2p_pairs": st["p2p_pairs"]}
+        h.close()
+    return {"mutual_1m": {
+        "workload": "uniform cube N=1048576, P=8, theta=0.5, ncrit=64, build + evaluate, L2 flushed: one-sided "
+                    "P2P vs the mutual near field (each unordered leaf pair once, both directions)",
+        "one_sided": out["one_sided"], "mutual": out["mutual"],
+        "mutual_vs_one_sided": out["one_sided"]["ms"] / out["mutual"]["ms"],
+        "p2p_phase_ratio": out["one_sided"]["p2p_ms"] / out["mutual"]["p2p_ms"]}}
 
 
 def variant_hybrid(torch, stream, flush):

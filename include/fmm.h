@@ -49,6 +49,9 @@ extern "C" {
 /* Flags for fmm_options.flags. */
 #define FMM_FLAG_KAHAN 1u         /* compensated (Kahan) P2P accumulation per target */
 #define FMM_FLAG_TIMING 2u        /* record per-phase device times (adds events) */
+#define FMM_FLAG_MUTUAL 4u        /* mutual near field: each unordered leaf pair of the P2P list once, both
+                                     directions (Newton's third law, the falcON heritage of Sec. 2); the
+                                     same lists and results to rounding, not bitwise (float reductions) */
 
 /* Largest number of charge vectors of one fmm_evaluate_batch call. */
 #define FMM_MAX_RHS 32

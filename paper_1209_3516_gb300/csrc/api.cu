@@ -231,7 +231,9 @@ int fmm_destroy(fmm_handle *w)
                       &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_poff, &h.p2p_ent, &h.p2p_cnt,
                       &h.pairs_count, &h.M, &h.L, &h.phi_sorted, &h.energy_part, &h.hx, &h.hq, &h.hphi, &h.hgrad,
                       &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb,
-                      &h.c_scale, &h.tc_items, &h.lbh, &h.lbl, &h.tc_next};
+                      &h.c_scale, &h.tc_items, &h.lbh, &h.lbl, &h.tc_next, &h.mu_off, &h.mu_src,
+                      &h.os_off, &h.os_src, &h.mu_cnt_tmp, &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent,
+                      &h.os_cnt, &h.racc};
     for (DevBuf *b : bufs) b->release();
     if (h.events_ready)
         for (auto &ev : h.ev) cudaEventDestroy(ev);

@@ -148,6 +148,14 @@ struct Handle {
     int64_t n_items = 0;
     int p2p_g = 0;             // targets per P2P work item (0: the default, 16; 8 on request)
     DevBuf pairs_count;        // u64 scratch (P2P particle-pair count)
+    // mutual schedule (FMM_FLAG_MUTUAL): the lists split into mutual entries
+    // (B > A, mirrored) and one-sided ones (CSR by cell), their source runs, and
+    // the accumulator of the mutual pass (float4 per sorted particle)
+    bool mutual_ready = false;
+    int64_t n_mutual = 0, n_onesided = 0, n_mu_runs = 0, n_os_runs = 0;
+    DevBuf mu_off, mu_src, os_off, os_src, mu_cnt_tmp;
+    DevBuf mu_poff, mu_ent, mu_cnt, os_poff, os_ent, os_cnt;
+    DevBuf racc;
 
     // expansions and outputs
     DevBuf M, L;          // float[ncells * TP]
@@ -205,6 +213,9 @@ int build_lists(Handle &h);                       // DTT + grouping
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
 int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items);   // items of <= g targets
 int p2p_batch_tc(Handle &h, int nrhs, float *phi, float *grad);   // batched P2P + L2P, tensor cores
+int build_runs(Handle &h, const int *off, const int *src, DevBuf &roff, DevBuf &ent, DevBuf &cnt, int64_t &nruns);
+int build_mutual(Handle &h);   // split the P2P lists for the mutual schedule
+int p2p_mutual(Handle &h);     // the mutual P2P pass (fills racc)
 
 int evaluate_upward(Handle &h, const float *q);   // gather q, P2M, M2M
 int evaluate_m2l(Handle &h, const float *M, float *L);

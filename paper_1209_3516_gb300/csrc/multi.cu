@@ -366,7 +366,7 @@ int fmm_multi_create(fmm_multi **mp, int nsys, const int64_t *N, int P, float th
     }
     // every system (and the merged problem) runs on the private stream, which
     // the graph is captured on; calls order it after the caller's stream
-    fmm_options so = {priv, dev, opt ? (opt->flags & ~FMM_FLAG_KAHAN & ~FMM_FLAG_TIMING) : 0u};
+    fmm_options so = {priv, dev, opt ? (opt->flags & ~FMM_FLAG_KAHAN & ~FMM_FLAG_TIMING & ~FMM_FLAG_MUTUAL) : 0u};
     m.nsys = nsys;
     m.N.assign(N, N + nsys);
     m.pbase.assign(nsys, 0);

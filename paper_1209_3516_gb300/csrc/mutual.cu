@@ -1,0 +1,321 @@
+// mutual.cu -- mutual (Newton's third law) near field: each unordered leaf pair once.
+//
+// The paper's method descends from falcON (Sec. 2), whose near field evaluates
+// every pair of leaves once and applies the interaction to both of them.  The
+// P2P lists that Algorithm 4 emits here are symmetric ((A, B) is listed iff
+// (B, A) is), so with FMM_FLAG_MUTUAL each target leaf's list is split into
+//   - its mutual part: sources B > A whose mirror entry (B, A) exists, and
+//   - its one-sided part: B == A, and any entry without a mirror (checked by
+//     a binary search in B's sorted list; none are expected).
+// The mutual pass takes, for every work item of A's targets and every source
+// particle s of its mutual runs, both directions of each pair term:
+//   phi_t += q_s / r,  grad_t += q_s (u_s - u_t) / r^3   (target side, registers)
+//   phi_s += q_t / r,  grad_s += q_t (u_t - u_s) / r^3   (reaction: the lane
+//                                                         holding s, over the item's targets)
+// and adds both into an accumulator in sorted order with vector float
+// reductions (red.global.add.v4.f32 / .v2.f32): the reaction once per (item,
+// source particle), the target side once per (item, target).  The ordinary P2P
+// kernel then runs over the one-sided runs and adds the accumulator before the
+// L2P and the scatter to caller order.  A pair term costs 18 packed FP32
+// instructions per four interactions (two targets, both directions) instead
+// of 13 per two, and one SFU rsqrt per two interactions.  The order of the
+// floating-point reductions is not fixed, so results are reproducible to
+// rounding, not bitwise.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_util.cuh"
+#include "fmm_internal.cuh"
+#include "p2p_common.cuh"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// list split
+// ---------------------------------------------------------------------------
+// Is a in the sorted list src[b0, b1)?
+__device__ __forceinline__ bool list_has(const int *src, int b0, int b1, int a)
+{
+    while (b0 < b1) {
+        const int m = (b0 + b1) >> 1;
+        const int v = src[m];
+        if (v == a) return true;
+        if (v < a) b0 = m + 1;
+        else b1 = m;
+    }
+    return false;
+}
+
+// 0: skip (the mirror's mutual entry covers it), 1: mutual, 2: one-sided
+__device__ __forceinline__ int mutual_kind(const int *off, const int *src, int a, int b)
+{
+    if (b == a) return 2;
+    const bool mirror = list_has(src, off[b], off[b + 1], a);
+    if (!mirror) return 2;
+    return b > a ? 1 : 0;
+}
+
+// One warp per leaf: counts of its mutual and one-sided entries.
+__global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned *cnt_mu,
+                               unsigned *cnt_os)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaves) return;
+    const int t = leaf_list[w];
+    const int eb = off[t], ee = off[t + 1];
+    unsigned nm = 0, no = 0;
+    for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + (int)lane_id();
+        const int k = e < ee ? mutual_kind(off, src, t, src[e]) : 0;
+        nm += __popc(__ballot_sync(kFull, k == 1));
+        no += __popc(__ballot_sync(kFull, k == 2));
+    }
+    if (lane_id() == 0) {
+        cnt_mu[t] = nm;
+        cnt_os[t] = no;
+    }
+}
+
+// One warp per leaf: its entries into the two lists, in list (source) order.
+__global__ void k_mutual_write(int nleaves, const int *leaf_list, const int *off, const int *src,
+                               const unsigned *mu_off, const unsigned *os_off, int *mu_src, int *os_src)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaves) return;
+    const unsigned lane = lane_id();
+    const int t = leaf_list[w];
+    const int eb = off[t], ee = off[t + 1];
+    unsigned pm = mu_off[t], po = os_off[t];
+    for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + (int)lane;
+        const int s = e < ee ? src[e] : 0;
+        const int k = e < ee ? mutual_kind(off, src, t, s) : 0;
+        const unsigned bm = __ballot_sync(kFull, k == 1), bo = __ballot_sync(kFull, k == 2);
+        if (k == 1) mu_src[pm + __popc(bm & lanemask_lt())] = s;
+        if (k == 2) os_src[po + __popc(bo & lanemask_lt())] = s;
+        pm += __popc(bm);
+        po += __popc(bo);
+    }
+}
+
+// Split the grouped P2P lists and build the source runs of both parts.
+int build_mutual(Handle &h)
+{
+    const int nl = (int)h.nleaves;
+    const int64_t nc = h.ncells;
+    FMM_TRY(h.mu_off.reserve((size_t)(nc + 1) * sizeof(unsigned)));
+    FMM_TRY(h.os_off.reserve((size_t)(nc + 1) * sizeof(unsigned)));
+    FMM_TRY(h.mu_cnt_tmp.reserve((size_t)(2 * nc) * sizeof(unsigned)));
+    unsigned *cm = h.mu_cnt_tmp.as<unsigned>(), *co = cm + nc;
+    FMM_CUDA(cudaMemsetAsync(cm, 0, (size_t)(2 * nc) * sizeof(unsigned), h.stream));
+    const int blocks = ceil_div((int64_t)nl * 32, 256);
+    ++h.launches;
+    k_mutual_count<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
+                                                 cm, co);
+    unsigned *mo = h.mu_off.as<unsigned>(), *oo = h.os_off.as<unsigned>();
+    FMM_TRY(scan_exclusive_u32(h, cm, mo, nc, mo + nc));
+    FMM_TRY(scan_exclusive_u32(h, co, oo, nc, oo + nc));
+    unsigned tot[2];
+    FMM_CUDA(cudaMemcpyAsync(&tot[0], mo + nc, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaMemcpyAsync(&tot[1], oo + nc, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
+    FMM_CUDA(cudaStreamSynchronize(h.stream));
+    h.n_mutual = tot[0];
+    h.n_onesided = tot[1];
+    FMM_TRY(h.mu_src.reserve(std::max<size_t>(tot[0], 1) * sizeof(int)));
+    FMM_TRY(h.os_src.reserve(std::max<size_t>(tot[1], 1) * sizeof(int)));
+    ++h.launches;
+    k_mutual_write<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
+                                                 mo, oo, h.mu_src.as<int>(), h.os_src.as<int>());
+    FMM_CHECK_LAUNCH("mutual list split");
+    FMM_TRY(build_runs(h, h.mu_off.as<int>(), h.mu_src.as<int>(), h.mu_poff, h.mu_ent, h.mu_cnt, h.n_mu_runs));
+    FMM_TRY(build_runs(h, h.os_off.as<int>(), h.os_src.as<int>(), h.os_poff, h.os_ent, h.os_cnt, h.n_os_runs));
+    FMM_TRY(h.racc.reserve((size_t)h.N * sizeof(float4)));
+    h.mutual_ready = true;
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mutual P2P pass
+// ---------------------------------------------------------------------------
+constexpr int kMuG = 16;           // targets per work item (the P2P items)
+constexpr int kMuThreads = 64;     // two warps per block
+constexpr int kMuSlots = 256;      // staged sources per buffer
+constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots * (int)sizeof(float4));
+
+__device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float *addr, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// Stage up to kMuSlots sources of the item's runs: positions (with charges) by
+// cp.async, the frame shift with the particle's index (as int bits in w).
+__device__ __forceinline__ int mu_stage(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
+                                        float4 *part, float4 *shift)
+{
+    const int lane = (int)lane_id();
+    int slots = 0;
+    while (slots < kMuSlots && cur.e < cur.e1) {
+        const int m = min(cur.cnt - cur.o, kMuSlots - slots);
+        const int begin = cur.pb + cur.o;
+        for (int i = lane; i < m; i += 32) {
+            cp_async16(part + slots + i, pos + begin + i);
+            shift[slots + i] = make_float4(cur.shx, cur.shy, cur.shz, __int_as_float(begin + i));
+        }
+        slots += m;
+        cur.o += m;
+        if (cur.o == cur.cnt) {
+            ++cur.e;
+            cur.o = 0;
+            cur.load(run, run_end);
+        }
+    }
+    return slots;
+}
+
+// Both directions of the pair terms of one source (in the target frame, charge
+// sq) with NT targets, two per packed instruction: ntx.. negated target
+// positions, nqt negated target charges; acc[4h + k] the target side, ps, gs
+// the source's reaction (ps accumulates -phi_s).
+template <int NT>
+__device__ __forceinline__ void mu_tile(const float4 &s, const float2 *ntx, const float2 *nty, const float2 *ntz,
+                                        const float2 *nqt, float2 *acc, float2 &ps, float2 &gsx, float2 &gsy,
+                                        float2 &gsz)
+{
+    constexpr float kEps = 1.17549435e-38f;
+    const float2 sx = make_float2(s.x, s.x), sy = make_float2(s.y, s.y), sz = make_float2(s.z, s.z);
+    const float2 sq = make_float2(s.w, s.w);
+    const float2 eps = make_float2(kEps, kEps);
+#pragma unroll
+    for (int h = 0; h < NT / 2; ++h) {
+        const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
+        float2 r2 = __ffma2_rn(dx, dx, eps);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+        // target side: phi_t += q_s / r, grad_t += q_s e / r^3
+        acc[4 * h + 0] = __ffma2_rn(sq, rinv, acc[4 * h + 0]);
+        const float2 qs3 = __fmul2_rn(sq, rinv3);
+        acc[4 * h + 1] = __ffma2_rn(qs3, dx, acc[4 * h + 1]);
+        acc[4 * h + 2] = __ffma2_rn(qs3, dy, acc[4 * h + 2]);
+        acc[4 * h + 3] = __ffma2_rn(qs3, dz, acc[4 * h + 3]);
+        // reaction: -phi_s += (-q_t) / r, grad_s += (-q_t) e / r^3
+        ps = __ffma2_rn(nqt[h], rinv, ps);
+        const float2 qt3 = __fmul2_rn(nqt[h], rinv3);
+        gsx = __ffma2_rn(qt3, dx, gsx);
+        gsy = __ffma2_rn(qt3, dy, gsy);
+        gsz = __ffma2_rn(qt3, dz, gsz);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
+                                          float4 *buf, const float2 *ntx, const float2 *nty, const float2 *ntz,
+                                          const float2 *nqt, float2 *acc, float4 *racc)
+{
+    const int lane = (int)lane_id();
+    int n_cur = mu_stage(cur, run, run_end, pos, buf, buf + kMuSlots);
+    cp_async_commit();
+    for (int c = 0; n_cur > 0; ++c) {
+        float4 *cur_part = buf + (c & 1) * (2 * kMuSlots);
+        float4 *cur_shift = cur_part + kMuSlots;
+        float4 *nx = buf + ((c + 1) & 1) * (2 * kMuSlots);
+        const int n_next = mu_stage(cur, run, run_end, pos, nx, nx + kMuSlots);
+        cp_async_commit();
+        cp_async_wait_1();
+        __syncwarp();
+        for (int t0 = 0; t0 < n_cur; t0 += 32) {
+            const int j = t0 + lane;
+            float4 s = make_float4(1e20f, 1e20f, 1e20f, 0.f);   // past the count: far away, no charge
+            int sidx = -1;
+            if (j < n_cur) {
+                s = cur_part[j];
+                const float4 d = cur_shift[j];
+                s.x += d.x;
+                s.y += d.y;
+                s.z += d.z;
+                sidx = __float_as_int(d.w);
+            }
+            float2 ps = make_float2(0.f, 0.f), gsx = ps, gsy = ps, gsz = ps;
+            mu_tile<NT>(s, ntx, nty, ntz, nqt, acc, ps, gsx, gsy, gsz);
+            if (sidx >= 0) red_add_v4(racc + sidx, -(ps.x + ps.y), gsx.x + gsx.y, gsy.x + gsy.y, gsz.x + gsz.y);
+        }
+        __syncwarp();   // every lane is done with this buffer before it is refilled
+        n_cur = n_next;
+    }
+}
+
+// One warp per work item (<= 16 targets of a leaf) over its mutual runs.
+__global__ void __launch_bounds__(kMuThreads, 4)
+    k_p2p_mutual(int nitems, const int4 *items, const unsigned *roff, const float4 *run, const int *run_end,
+                 const float4 *pos, float4 *racc)
+{
+    extern __shared__ float4 mu_smem[];
+    const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (item >= nitems) return;
+    const unsigned lane = lane_id();
+    float4 *buf = mu_smem + (threadIdx.x >> 5) * (4 * kMuSlots);
+    const int4 it = items[item];
+    const int tb = it.y, tc = it.z;
+    RunCursor cur;
+    cur.init(roff, it.w, run, run_end);
+    if (cur.e >= cur.e1) return;   // no mutual sources
+    // targets (negated positions and charges, float2 pairs); slots past the
+    // count repeat the last target's position with charge 0 (no reaction)
+    float2 ntx[kMuG / 2], nty[kMuG / 2], ntz[kMuG / 2], nqt[kMuG / 2];
+#pragma unroll
+    for (int h = 0; h < kMuG / 2; ++h) {
+        const float4 p0 = pos[tb + min(2 * h, tc - 1)];
+        const float4 p1 = pos[tb + min(2 * h + 1, tc - 1)];
+        ntx[h] = make_float2(-p0.x, -p1.x);
+        nty[h] = make_float2(-p0.y, -p1.y);
+        ntz[h] = make_float2(-p0.z, -p1.z);
+        nqt[h] = make_float2(2 * h < tc ? -p0.w : 0.0f, 2 * h + 1 < tc ? -p1.w : 0.0f);
+    }
+    float2 a[2 * kMuG];
+#pragma unroll
+    for (int i = 0; i < 2 * kMuG; ++i) a[i] = make_float2(0.0f, 0.0f);
+    const int ntr = tc <= 4 ? 4 : tc <= 8 ? 8 : tc <= 12 ? 12 : 16;
+    if (ntr == 4) mu_stream<4>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
+    else if (ntr == 8) mu_stream<8>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
+    else if (ntr == 12) mu_stream<12>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
+    else mu_stream<16>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
+    // target side: reduce-scatter, lanes 2g / 2g + 1 add (phi, gx) / (gy, gz) of target g
+    float v[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+#pragma unroll
+    for (int h = 0; h < kMuG / 2; ++h)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[4 * (2 * h) + k] = a[4 * h + k].x;
+            v[4 * (2 * h + 1) + k] = a[4 * h + k].y;
+        }
+    warp_reduce_scatter64(v);
+    const int g = (int)(lane >> 1);
+    if (g < tc) red_add_v2(reinterpret_cast<float *>(racc + tb + g) + 2 * (lane & 1u), v[0], v[1]);
+}
+
+int p2p_mutual(Handle &h)
+{
+    static bool configured[64] = {};
+    if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
+        FMM_CUDA(cudaFuncSetAttribute(k_p2p_mutual, cudaFuncAttributeMaxDynamicSharedMemorySize, kMuSmem));
+        configured[h.device] = true;
+    }
+    FMM_CUDA(cudaMemsetAsync(h.racc.p, 0, (size_t)h.N * sizeof(float4), h.stream));
+    ++h.launches;
+    k_p2p_mutual<<<ceil_div((int64_t)h.n_items * 32, kMuThreads), kMuThreads, kMuSmem, h.stream>>>(
+        (int)h.n_items, h.p2p_items.as<int4>(), h.mu_poff.as<unsigned>(), h.mu_ent.as<float4>(), h.mu_cnt.as<int>(),
+        h.pos.as<float4>(), h.racc.as<float4>());
+    FMM_CHECK_LAUNCH("mutual p2p");
+    return FMM_OK;
+}
+
+}  // namespace fmm

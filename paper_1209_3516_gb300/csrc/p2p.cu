@@ -148,25 +148,6 @@ __global__ void k_p2p_runs(int nleaves, const int *leaf_list, const int *off, co
     }
 }
 
-// Reduce-scatter 64 values across the warp by recursive halving: on return
-// lane l holds entries 2l and 2l+1 of the warp-wide sums.
-__device__ __forceinline__ void warp_reduce_scatter64(float *v)
-{
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int step = 0; step < 5; ++step) {
-        const int half = 32 >> step;          // values kept after this step
-        const unsigned mask = 16u >> step;
-        const bool upper = (lane & mask) != 0u;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const float send = upper ? v[i] : v[i + half];
-            const float keep = upper ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
-        }
-    }
-}
-
 // Accumulate the interactions of one source s (already in the target frame) with
 // NT targets, two targets per packed FP32 instruction (FFMA2 / FADD2 / FMUL2):
 // targets are held negated as float2 pairs (ntx[h] = -(t_2h, t_2h+1)), and
@@ -310,8 +291,8 @@ __device__ __forceinline__ bool p2p_stream(RunCursor &cur, const float4 *run, co
 
 template <int P, bool kKahan, int G>
 __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nitems, const int4 *items, const unsigned *roff,
-                                                     const float4 *run, const int *run_end, const float4 *pos,
-                                                     const int *pbeg, const int *pcnt, const int *level,
+                                                     const float4 *run, const int *run_end, const float4 *racc,
+                                                     const float4 *pos, const int *pbeg, const int *pcnt, const int *level,
                                                      const int *parent, const float4 *geom, const float *L,
                                                      const int *perm, float phi_scale, float grad_scale,
                                                      const float2 *cell_scale, float *phi, float *grad,
@@ -409,6 +390,13 @@ __global__ void __launch_bounds__(kP2PThreads, FMM_P2P_MIN_BLOCKS) k_p2p(int nit
     const int sidx = tb + g;
     const float4 p = pos[sidx];
     float pot = v[0], gx = v[1], gy = o0, gz = o1;
+    if (racc) {   // the mutual pass's sums for this target
+        const float4 r = racc[sidx];
+        pot += r.x;
+        gx += r.y;
+        gy += r.z;
+        gz += r.w;
+    }
 
     // L2P: phi += sum_n Lb_n w_n(r / s), grad += (1/s) sum_m Lb_{m + e_d} w_m(r / s),
     // r = u - X_leaf = d - (X_leaf - X_frame)
@@ -476,29 +464,40 @@ int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items)
     return FMM_OK;
 }
 
-int build_p2p_items(Handle &h)
+// Source runs of the lists (off, src) of every leaf: run offsets per leaf-list
+// entry (roff, nleaves + 1), run records and end particles; *nruns their count.
+int build_runs(Handle &h, const int *off, const int *src, DevBuf &roff_buf, DevBuf &ent, DevBuf &cnt,
+               int64_t &nruns)
 {
     const int nl = (int)h.nleaves;
     FMM_TRY(h.c_tmp.reserve((size_t)(nl + 1) * sizeof(unsigned)));
     unsigned *nrun = h.c_tmp.as<unsigned>();
-    FMM_TRY(h.p2p_poff.reserve((size_t)(nl + 1) * sizeof(unsigned)));
-    unsigned *roff = h.p2p_poff.as<unsigned>();
-    // source runs of every target leaf's list
+    FMM_TRY(roff_buf.reserve((size_t)(nl + 1) * sizeof(unsigned)));
+    unsigned *roff = roff_buf.as<unsigned>();
     ++h.launches;
     k_p2p_run_count<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
-        nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.c_parent.as<int>(), h.c_pbeg.as<int>(),
-        h.c_pcnt.as<int>(), nrun);
+        nl, h.leaf_list.as<int>(), off, src, h.c_parent.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), nrun);
     FMM_TRY(scan_exclusive_u32(h, nrun, roff, nl, roff + nl));
     FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, roff + nl, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
     FMM_CUDA(cudaStreamSynchronize(h.stream));
-    h.n_pieces = h.pinned->level_total;
-    FMM_TRY(h.p2p_ent.reserve(std::max<int64_t>(h.n_pieces, 1) * sizeof(float4)));
-    FMM_TRY(h.p2p_cnt.reserve(std::max<int64_t>(h.n_pieces, 1) * sizeof(int)));
+    nruns = h.pinned->level_total;
+    FMM_TRY(ent.reserve(std::max<int64_t>(nruns, 1) * sizeof(float4)));
+    FMM_TRY(cnt.reserve(std::max<int64_t>(nruns, 1) * sizeof(int)));
     ++h.launches;
     k_p2p_runs<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
-        nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.c_parent.as<int>(), h.c_pbeg.as<int>(),
-        h.c_pcnt.as<int>(), h.c_geom.as<float4>(), roff, h.p2p_ent.as<float4>(), h.p2p_cnt.as<int>());
+        nl, h.leaf_list.as<int>(), off, src, h.c_parent.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(),
+        h.c_geom.as<float4>(), roff, ent.as<float4>(), cnt.as<int>());
     FMM_CHECK_LAUNCH("p2p runs");
+    return FMM_OK;
+}
+
+int build_p2p_items(Handle &h)
+{
+    // source runs of every target leaf's list
+    FMM_TRY(build_runs(h, h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.p2p_poff, h.p2p_ent, h.p2p_cnt, h.n_pieces));
+    // the mutual schedule's split of the lists
+    h.mutual_ready = false;
+    if (h.flags & FMM_FLAG_MUTUAL) FMM_TRY(build_mutual(h));
     // work items (the adjoint's items are built on first use)
     h.adj_items_ready = false;
     h.tc_items_ready = false;
@@ -517,9 +516,13 @@ template <int P, bool kKahan, int G> static int p2p_launch(Handle &h, float *phi
     const float grad_scale = (float)(1.0 / (h.norm_host[3] * h.norm_host[3]));
     const int blocks = ceil_div((int64_t)h.n_items * 32, kP2PThreads);
     ++h.launches;
+    // with the mutual schedule this pass covers the one-sided entries and adds
+    // the accumulated mutual sums
+    const bool mu = h.mutual_ready;
     k_p2p<P, kKahan, G><<<blocks, kP2PThreads, kP2PSmem, h.stream>>>(
-        (int)h.n_items, h.p2p_items.as<int4>(), h.p2p_poff.as<unsigned>(), h.p2p_ent.as<float4>(),
-        h.p2p_cnt.as<int>(), h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
+        (int)h.n_items, h.p2p_items.as<int4>(), (mu ? h.os_poff : h.p2p_poff).as<unsigned>(),
+        (mu ? h.os_ent : h.p2p_ent).as<float4>(), (mu ? h.os_cnt : h.p2p_cnt).as<int>(),
+        mu ? h.racc.as<float4>() : nullptr, h.pos.as<float4>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), h.c_level.as<int>(),
         h.c_parent.as<int>(), h.c_geom.as<float4>(), h.L.as<float>(), h.perm.as<int>(), phi_scale, grad_scale,
         h.c_scale.as<float2>(), phi, grad, h.phi_sorted.as<float>(), h.err_flag.as<unsigned>());
     FMM_CHECK_LAUNCH("p2p");
@@ -538,6 +541,7 @@ template <int P> static int p2p_impl(Handle &h, float *phi, float *grad)
 int evaluate_p2p(Handle &h, float *phi, float *grad)
 {
     FMM_TRY(h.phi_sorted.reserve(h.N * sizeof(float)));
+    if (h.mutual_ready) FMM_TRY(p2p_mutual(h));
     switch (h.P) {
     case 3: return p2p_impl<3>(h, phi, grad);
     case 4: return p2p_impl<4>(h, phi, grad);

@@ -161,4 +161,23 @@ struct RunCursor {
     }
 };
 
+// Reduce-scatter 64 values across the warp by recursive halving: on return
+// lane l holds entries 2l and 2l+1 of the warp-wide sums.
+__device__ __forceinline__ void warp_reduce_scatter64(float *v)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int half = 32 >> step;          // values kept after this step
+        const unsigned mask = 16u >> step;
+        const bool upper = (lane & mask) != 0u;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+    }
+}
+
 }  // namespace fmm

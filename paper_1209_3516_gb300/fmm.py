@@ -23,6 +23,7 @@ FMM_ERR_CAPACITY = -7
 
 FMM_FLAG_KAHAN = 1
 FMM_FLAG_TIMING = 2
+FMM_FLAG_MUTUAL = 4
 
 PHASES = ["morton", "sort", "tree", "traverse", "lists", "upward", "m2l", "downward", "p2p"]
 
@@ -203,7 +204,7 @@ class FMM:
     """A handle: fmm_create(N, P, theta, ncrit) on the current CUDA device and stream."""
 
     def __init__(self, N, P=4, theta=0.4, ncrit=64, kahan=False, timing=False, stream=None, device=None,
-                 hybrid=None):
+                 hybrid=None, mutual=False):
         import torch
         L = load()
         if device is None:
@@ -213,7 +214,8 @@ class FMM:
         self.stream = stream
         self.device = int(device)
         opt = _Options(ctypes.c_void_p(stream.cuda_stream), self.device,
-                       (FMM_FLAG_KAHAN if kahan else 0) | (FMM_FLAG_TIMING if timing else 0))
+                       (FMM_FLAG_KAHAN if kahan else 0) | (FMM_FLAG_TIMING if timing else 0) |
+                       (FMM_FLAG_MUTUAL if mutual else 0))
         h = _vp()
         _check(L.fmm_create(ctypes.byref(h), int(N), int(P), float(theta), int(ncrit), ctypes.byref(opt)))
         self._h = h
