@@ -39,6 +39,7 @@ METRIC = "FMM evals/s & P2P Gpair/s at N=1M, rel err 1e-4, vs plain FP32 path"
 FLOPS_PER_PAIR = 20          # the paper's count for a potential + force interaction (Table 4)
 FP32_LANES_PER_SM = 128
 P2P_FP32_OPS_PER_PAIR = 13   # 3 sub, 3 FMA (r^2), 3 mul, 1 add, 3 FMA: the P2P kernel's FP32 work per pair
+P2P_MUTUAL_FP32_OPS_PER_PAIR = 9   # mutual: 18 per pair term, which serves both directions (two interactions)
 
 
 def parse():
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--ncrit", type=int, default=64)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "plummer"])
     ap.add_argument("--kahan", action="store_true", help="compensated P2P accumulation")
+    ap.add_argument("--one-sided", action="store_true",
+                    help="one-sided near field (every listed leaf pair evaluated for its target only); the default "
+                         "is the mutual near field: each unordered leaf pair once, both directions")
     ap.add_argument("--hybrid", type=int, default=None,
                     help="M2L / P2P hybrid at the leaves: MAC-passing leaf pairs with at least this many "
                          "particle pairs go to M2L (default: Algorithm 4 as printed)")
@@ -84,6 +88,7 @@ def config(a):
             "N": a.N, "P": a.P, "theta": a.theta, "ncrit": a.ncrit, "dist": a.dist, "kahan": a.kahan,
             "hybrid_min_pairs": a.hybrid,
             "traversal": "Algorithm 4 as printed" if a.hybrid is None else "M2L / P2P hybrid at the leaves",
+            "near_field": "one-sided" if a.one_sided else "mutual (each unordered leaf pair once, both directions)",
             "step": "fmm_build + fmm_evaluate",
             "l2": "flushed before every timed step (256 MiB write)"}
 
@@ -142,6 +147,8 @@ def p2p_traffic(a):
         if (pj.get("N"), pj.get("P"), pj.get("theta"), pj.get("ncrit")) != (a.N, a.P, a.theta, a.ncrit):
             return None
         if (pj.get("dist", "uniform"), pj.get("kahan", False), pj.get("hybrid")) != (a.dist, a.kahan, a.hybrid):
+            return None
+        if pj.get("mutual", False) != (not a.one_sided):
             return None
         h = hashlib.sha256()
         for f in pj["sources"]:
@@ -570,7 +577,7 @@ def run_ours(a):
     phi = torch.empty(a.N, dtype=torch.float32, device="cuda")
     grad = torch.empty(a.N, 3, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, kahan=a.kahan, timing=True, hybrid=a.hybrid)
+    h = fmm.FMM(a.N, a.P, a.theta, a.ncrit, kahan=a.kahan, timing=True, hybrid=a.hybrid, mutual=not a.one_sided)
 
     def step():
         h.build(xd)
@@ -627,6 +634,9 @@ def run_ours(a):
     pk_clocks = pk_sampler.stop()
     peak_tflops = max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
     pair_rate = pairs / (p2p_mean * 1e-3)
+    # FP32 operations and SFU rsqrts per interaction of the near field as run
+    ops_per_pair = P2P_FP32_OPS_PER_PAIR if a.one_sided else P2P_MUTUAL_FP32_OPS_PER_PAIR
+    rsq_per_pair = 1.0 if a.one_sided else 0.5
     # M2L: the truncated contraction's flops per cell pair (2 C(P+5, 6)), both launches
     m2l_mean = statistics.mean(m2l_ms)
     m2l_flops = 2 * comb(a.P + 5, 6) * st["n_m2l"]
@@ -662,7 +672,8 @@ def run_ours(a):
                 "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(a),
                 "p2p_gpair_s": gpair_s,
-                "roofline": {"kernel": "k_p2p", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                "roofline": {"kernel": "k_p2p" if a.one_sided else "k_p2p_mutual + k_p2p (one-sided entries)",
+                             "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                              "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                              "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
                              "launch_ms": p2p_mean,
@@ -671,12 +682,14 @@ def run_ours(a):
                                            "events), FP32 FMA peak = the faster of the two; nominal %d SMs x 128 "
                                            "lanes x 2 x %.0f MHz = %.1f TFLOP/s" % (sms, sm_max, nominal_tflops),
                              "measured_peaks": dict(peaks, clocks=pk_clocks),
-                             "fp32_pipe_frac": pair_rate * P2P_FP32_OPS_PER_PAIR / (peak_tflops * 1e12 / 2),
-                             "sfu_frac": pair_rate / peaks["rsqrt_per_s"],
-                             "pipe_note": "fp32_pipe_frac: %d FP32 operations per pair (3 sub, 3 FMA for r^2, 3 mul, "
-                                          "1 add, 3 FMA) against the measured FMA operation rate; sfu_frac: one "
-                                          "rsqrt per pair against the measured SFU rsqrt rate"
-                                          % P2P_FP32_OPS_PER_PAIR},
+                             "fp32_pipe_frac": pair_rate * ops_per_pair / (peak_tflops * 1e12 / 2),
+                             "sfu_frac": pair_rate * rsq_per_pair / peaks["rsqrt_per_s"],
+                             "pipe_note": "pairs = target-source particle pairs of the P2P list (each interaction "
+                                          "once); fp32_pipe_frac: %d FP32 operations per interaction against the "
+                                          "measured FMA operation rate (one-sided: 3 sub, 3 FMA for r^2, 3 mul, 1 "
+                                          "add, 3 FMA = 13; mutual: 18 per pair term serving two interactions); "
+                                          "sfu_frac: %.1f rsqrt per interaction against the measured SFU rate"
+                                          % (ops_per_pair, rsq_per_pair)},
                 "m2l_roofline": {"kernel": "k_m2l", "bound": "alu", "unit": "TFLOP/s",
                                  "achieved": m2l_flops / (m2l_mean * 1e-3) / 1e12, "peak": peak_tflops,
                                  "frac": m2l_flops / (m2l_mean * 1e-3) / 1e12 / peak_tflops,

@@ -142,6 +142,9 @@ constexpr int kMuG = 16;           // targets per work item (the P2P items)
 constexpr int kMuThreads = 64;     // two warps per block
 constexpr int kMuSlots = 256;      // staged sources per buffer
 constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots * (int)sizeof(float4));
+#ifndef FMM_MU_MIN_BLOCKS
+#define FMM_MU_MIN_BLOCKS 4
+#endif
 
 __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d)
 {
@@ -252,7 +255,7 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
 }
 
 // One warp per work item (<= 16 targets of a leaf) over its mutual runs.
-__global__ void __launch_bounds__(kMuThreads, 4)
+__global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
     k_p2p_mutual(int nitems, const int4 *items, const unsigned *roff, const float4 *run, const int *run_end,
                  const float4 *pos, float4 *racc)
 {
