@@ -56,9 +56,10 @@ __device__ __forceinline__ int mutual_kind(const int *off, const int *src, int a
     return b > a ? 1 : 0;
 }
 
-// One warp per leaf: counts of its mutual and one-sided entries.
-__global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned *cnt_mu,
-                               unsigned *cnt_os)
+// One warp per leaf: the kind of each of its entries (kept for the write pass)
+// and its counts of mutual and one-sided entries.
+__global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned char *kind,
+                               unsigned *cnt_mu, unsigned *cnt_os)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nleaves) return;
@@ -68,6 +69,7 @@ __global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off
     for (int e0 = eb; e0 < ee; e0 += 32) {
         const int e = e0 + (int)lane_id();
         const int k = e < ee ? mutual_kind(off, src, t, src[e]) : 0;
+        if (e < ee) kind[e] = (unsigned char)k;
         nm += __popc(__ballot_sync(kFull, k == 1));
         no += __popc(__ballot_sync(kFull, k == 2));
     }
@@ -79,7 +81,8 @@ __global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off
 
 // One warp per leaf: its entries into the two lists, in list (source) order.
 __global__ void k_mutual_write(int nleaves, const int *leaf_list, const int *off, const int *src,
-                               const unsigned *mu_off, const unsigned *os_off, int *mu_src, int *os_src)
+                               const unsigned char *kind, const unsigned *mu_off, const unsigned *os_off, int *mu_src,
+                               int *os_src)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nleaves) return;
@@ -90,7 +93,7 @@ __global__ void k_mutual_write(int nleaves, const int *leaf_list, const int *off
     for (int e0 = eb; e0 < ee; e0 += 32) {
         const int e = e0 + (int)lane;
         const int s = e < ee ? src[e] : 0;
-        const int k = e < ee ? mutual_kind(off, src, t, s) : 0;
+        const int k = e < ee ? kind[e] : 0;
         const unsigned bm = __ballot_sync(kFull, k == 1), bo = __ballot_sync(kFull, k == 2);
         if (k == 1) mu_src[pm + __popc(bm & lanemask_lt())] = s;
         if (k == 2) os_src[po + __popc(bo & lanemask_lt())] = s;
@@ -106,13 +109,14 @@ int build_mutual(Handle &h)
     const int64_t nc = h.ncells;
     FMM_TRY(h.mu_off.reserve((size_t)(nc + 1) * sizeof(unsigned)));
     FMM_TRY(h.os_off.reserve((size_t)(nc + 1) * sizeof(unsigned)));
-    FMM_TRY(h.mu_cnt_tmp.reserve((size_t)(2 * nc) * sizeof(unsigned)));
+    FMM_TRY(h.mu_cnt_tmp.reserve((size_t)(2 * nc) * sizeof(unsigned) + (size_t)std::max<int64_t>(h.n_p2p, 1)));
     unsigned *cm = h.mu_cnt_tmp.as<unsigned>(), *co = cm + nc;
+    unsigned char *kind = reinterpret_cast<unsigned char *>(co + nc);   // one byte per list entry
     FMM_CUDA(cudaMemsetAsync(cm, 0, (size_t)(2 * nc) * sizeof(unsigned), h.stream));
     const int blocks = ceil_div((int64_t)nl * 32, 256);
     ++h.launches;
     k_mutual_count<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
-                                                 cm, co);
+                                                 kind, cm, co);
     unsigned *mo = h.mu_off.as<unsigned>(), *oo = h.os_off.as<unsigned>();
     FMM_TRY(scan_exclusive_u32(h, cm, mo, nc, mo + nc));
     FMM_TRY(scan_exclusive_u32(h, co, oo, nc, oo + nc));
@@ -126,7 +130,7 @@ int build_mutual(Handle &h)
     FMM_TRY(h.os_src.reserve(std::max<size_t>(tot[1], 1) * sizeof(int)));
     ++h.launches;
     k_mutual_write<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
-                                                 mo, oo, h.mu_src.as<int>(), h.os_src.as<int>());
+                                                 kind, mo, oo, h.mu_src.as<int>(), h.os_src.as<int>());
     FMM_CHECK_LAUNCH("mutual list split");
     FMM_TRY(build_runs(h, h.mu_off.as<int>(), h.mu_src.as<int>(), h.mu_poff, h.mu_ent, h.mu_cnt, h.n_mu_runs));
     FMM_TRY(build_runs(h, h.os_off.as<int>(), h.os_src.as<int>(), h.os_poff, h.os_ent, h.os_cnt, h.n_os_runs));
