@@ -251,9 +251,10 @@ int fmm_energy_noalloc(const float *q, const float *phi, int64_t n, double *E, v
  * launch over all systems: one charge gather, one P2M, one M2M and one L2L per
  * level, one M2L and one P2P.  fmm_multi_evaluate captures that evaluation into
  * a CUDA graph on first use (after an eager run that sizes the buffers and an
- * autotuner that times the P2P kernel with 16- and 8-target work items on the
- * merged problem and keeps the faster) and replays the graph afterwards; new
- * q / phi / grad pointers trigger a new capture.
+ * autotuner that times the near field on the merged problem in four
+ * configurations -- work items of 16 or 8 targets, one-sided or mutual -- and
+ * keeps the fastest) and replays the graph afterwards; new q / phi / grad
+ * pointers trigger a new capture.
  */
 typedef struct fmm_multi fmm_multi;
 
@@ -264,9 +265,10 @@ struct fmm_multi_info {
     int64_t graph_nodes;           /* kernel nodes of the captured evaluation */
     int64_t kernel_launches;       /* kernels launched on the merged problem (merge, tuning, eager runs) */
     int32_t nsys, nlevels;
-    int32_t p2p_targets_per_item;  /* the autotuner's choice */
-    int32_t reserved;
-    double tune_ms[2];             /* P2P kernel time with 16 and with 8 targets per item */
+    int32_t p2p_targets_per_item;  /* the autotuner's choice (or the pinned one) */
+    int32_t mutual;                /* 1: the mutual near field was chosen (or pinned) */
+    double tune_ms[4];             /* near-field time: one-sided 16, one-sided 8, mutual 16, mutual 8 targets
+                                      per item (best of 3 each) */
     double ms_evaluate;            /* device time of the last graph replay */
 };
 
@@ -292,6 +294,14 @@ int fmm_multi_evaluate(fmm_multi *m, const float *q, float *phi, float *grad);
 
 /* fmm_multi_set_hybrid -- fmm_set_hybrid for every system, for the next fmm_multi_build. */
 int fmm_multi_set_hybrid(fmm_multi *m, int64_t min_pairs);
+
+/*
+ * fmm_multi_set_config -- pin the near-field configuration instead of letting
+ * the autotuner choose: targets_per_item 0 (tune), 8 or 16; mutual -1 (tune),
+ * 0 (one-sided) or 1 (mutual).  Applied at the next fmm_multi_evaluate (the
+ * table is still timed and reported by fmm_multi_info).
+ */
+int fmm_multi_set_config(fmm_multi *m, int targets_per_item, int mutual);
 
 /* fmm_multi_info -- sizes, the autotuner's timings and choice, the last replay's time (HOST *info). */
 int fmm_multi_info(fmm_multi *m, struct fmm_multi_info *info);

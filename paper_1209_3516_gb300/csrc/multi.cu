@@ -9,9 +9,10 @@
 // systems: one charge gather, one P2M, one M2M and one L2L launch per level,
 // one M2L and one P2P launch in total, whatever the number of systems.
 // That evaluation is captured into a CUDA graph once and replayed, so a call
-// costs one graph launch.  Before capture a small autotuner times the P2P
-// kernel with work items of 16 and of 8 targets on the merged problem and
-// keeps the faster.
+// costs one graph launch.  Before capture an autotuner times the near field on
+// the merged problem in four configurations -- work items of 16 or 8 targets,
+// one-sided or mutual (each unordered leaf pair once, both directions) -- and
+// keeps the fastest (fmm_multi_set_config can pin either choice).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +45,15 @@ __global__ void k_merge_cells(int nc, const int *level, const int *pbeg, const i
     m_m2l_count[nw] = (unsigned)(m2l_off[c + 1] - m2l_off[c]);
 }
 
-// warp per cell: copy its M2L sources to the merged list, renumbered
+// per cell: its list length (cell-indexed CSR offsets) at its merged index
+__global__ void k_merge_count(int nc, const int *level, const int *map_base, const int *off, unsigned *m_count)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    m_count[c + map_base[level[c]]] = (unsigned)(off[c + 1] - off[c]);
+}
+
+// warp per cell: copy its list (M2L or P2P sources) to the merged list, renumbered
 __global__ void k_merge_m2l(int nc, const int *level, const int *map_base, const int *m2l_off, const int *m2l_src,
                             const unsigned *m_off, int *m_src)
 {
@@ -100,7 +109,10 @@ struct Multi {
     const float *g_q = nullptr;
     float *g_phi = nullptr, *g_grad = nullptr;
     bool merged = false, tuned = false, timed = false;
-    float tune_ms[2] = {0.f, 0.f};  // P2P with 16 and with 8 targets per item
+    // P2P phase time per configuration: one-sided with 16 / 8 targets per item,
+    // mutual with 16 / 8 (the autotuner's table)
+    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
+    int pin_g = 0, pin_mutual = -1;   // fmm_multi_set_config (0 / -1: tune)
     int64_t n_m2l = 0, p2p_pairs = 0;
 };
 
@@ -108,7 +120,9 @@ static void release_merged(Handle &h)
 {
     DevBuf *bufs[] = {&h.pos, &h.perm, &h.c_level, &h.c_pbeg, &h.c_pcnt, &h.c_cbeg, &h.c_ccnt, &h.c_parent,
                       &h.c_geom, &h.c_scale, &h.m2l_off, &h.m2l_src, &h.leaf_list, &h.p2p_poff, &h.p2p_ent,
-                      &h.p2p_cnt, &h.p2p_items, &h.M, &h.L, &h.phi_sorted, &h.c_tmp, &h.scan_tmp};
+                      &h.p2p_cnt, &h.p2p_items, &h.M, &h.L, &h.phi_sorted, &h.c_tmp, &h.scan_tmp,
+                      &h.p2p_off, &h.p2p_src, &h.mu_off, &h.mu_src, &h.os_off, &h.os_src, &h.mu_cnt_tmp,
+                      &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent, &h.os_cnt, &h.racc};
     for (DevBuf *b : bufs) b->release();
 }
 
@@ -213,6 +227,32 @@ static int merge_systems(Multi &m)
                                                                             hm.m2l_off.as<unsigned>(),
                                                                             hm.m2l_src.as<int>());
     }
+    // merged P2P CSR (the mutual schedule splits it), the same way
+    FMM_TRY(hm.p2p_off.reserve((C + 1) * sizeof(unsigned)));
+    int64_t np2p = 0;
+    for (int s = 0; s < S; ++s) {
+        Handle &h = m.sys[s]->h;
+        const int *mb = map_dev.as<int>() + (size_t)s * (L + 2) + 1;
+        const int nc = (int)h.ncells;
+        ++hm.launches;
+        k_merge_count<<<ceil_div(nc, 256), 256, 0, hm.stream>>>(nc, h.c_level.as<int>(), mb, h.p2p_off.as<int>(),
+                                                                mcount);
+        np2p += h.n_p2p;
+    }
+    FMM_TRY(scan_exclusive_u32(hm, mcount, hm.p2p_off.as<unsigned>(), C, hm.p2p_off.as<unsigned>() + C));
+    FMM_TRY(hm.p2p_src.reserve(std::max<int64_t>(np2p, 1) * sizeof(int)));
+    for (int s = 0; s < S; ++s) {
+        Handle &h = m.sys[s]->h;
+        const int *mb = map_dev.as<int>() + (size_t)s * (L + 2) + 1;
+        const int nc = (int)h.ncells;
+        ++hm.launches;
+        k_merge_m2l<<<ceil_div((int64_t)nc * 32, 256), 256, 0, hm.stream>>>(nc, h.c_level.as<int>(), mb,
+                                                                            h.p2p_off.as<int>(), h.p2p_src.as<int>(),
+                                                                            hm.p2p_off.as<unsigned>(),
+                                                                            hm.p2p_src.as<int>());
+    }
+    hm.n_p2p = np2p;
+    hm.mutual_ready = false;
     FMM_CHECK_LAUNCH("merge systems");
     FMM_CUDA(cudaStreamSynchronize(hm.stream));
     map_dev.release();
@@ -241,29 +281,49 @@ static int merged_evaluate(Handle &hm, const float *q, float *phi, float *grad)
     return evaluate_p2p(hm, phi, grad);
 }
 
-// Time the P2P kernel with 16- and 8-target work items on the merged problem
-// (the far field of this call is in place) and keep the faster.
+// Best of 3 timed P2P phases (after one warm-up) of the current configuration.
+static int time_p2p(Multi &m, float *phi, float *grad, float *best_ms)
+{
+    Handle &hm = m.hm;
+    FMM_TRY(evaluate_p2p(hm, phi, grad));   // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        FMM_CUDA(cudaEventRecord(m.ev_t0, hm.stream));
+        FMM_TRY(evaluate_p2p(hm, phi, grad));
+        FMM_CUDA(cudaEventRecord(m.ev_t1, hm.stream));
+        FMM_CUDA(cudaEventSynchronize(m.ev_t1));
+        float ms = 0.f;
+        FMM_CUDA(cudaEventElapsedTime(&ms, m.ev_t0, m.ev_t1));
+        best = std::min(best, ms);
+    }
+    *best_ms = best;
+    return FMM_OK;
+}
+
+// The tile autotuner of the merged problem (the far field of this call is in
+// place): the near field with work items of 16 and of 8 targets, one-sided
+// and mutual, each timed on the merged problem; the fastest is kept, unless
+// fmm_multi_set_config pinned a choice.
 static int autotune(Multi &m, float *phi, float *grad)
 {
     Handle &hm = m.hm;
     const int gs[2] = {16, 8};
-    for (int k = 0; k < 2; ++k) {
-        hm.p2p_g = gs[k];
-        FMM_TRY(build_work_items(hm, gs[k], hm.p2p_items, hm.n_items));
-        FMM_TRY(evaluate_p2p(hm, phi, grad));   // warm-up
-        float best = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-            FMM_CUDA(cudaEventRecord(m.ev_t0, hm.stream));
-            FMM_TRY(evaluate_p2p(hm, phi, grad));
-            FMM_CUDA(cudaEventRecord(m.ev_t1, hm.stream));
-            FMM_CUDA(cudaEventSynchronize(m.ev_t1));
-            float ms = 0.f;
-            FMM_CUDA(cudaEventElapsedTime(&ms, m.ev_t0, m.ev_t1));
-            best = std::min(best, ms);
+    for (int mu = 0; mu < 2; ++mu) {
+        if (mu) FMM_TRY(build_mutual(hm));
+        hm.mutual_ready = mu != 0;
+        for (int k = 0; k < 2; ++k) {
+            hm.p2p_g = gs[k];
+            FMM_TRY(build_work_items(hm, gs[k], hm.p2p_items, hm.n_items));
+            FMM_TRY(time_p2p(m, phi, grad, &m.tune_ms[2 * mu + k]));
         }
-        m.tune_ms[k] = best;
     }
-    const int g = m.tune_ms[1] < m.tune_ms[0] ? 8 : 16;
+    int best = 0;
+    for (int i = 1; i < 4; ++i)
+        if (m.tune_ms[i] < m.tune_ms[best]) best = i;
+    int mu = best >> 1, g = gs[best & 1];
+    if (m.pin_mutual >= 0) mu = m.pin_mutual;
+    if (m.pin_g) g = m.pin_g;
+    hm.mutual_ready = mu != 0;
     hm.p2p_g = g;
     FMM_TRY(build_work_items(hm, g, hm.p2p_items, hm.n_items));
     m.tuned = true;
@@ -491,6 +551,26 @@ int fmm_multi_set_hybrid(fmm_multi *w, int64_t min_pairs)
     return FMM_OK;
 }
 
+int fmm_multi_set_config(fmm_multi *w, int targets_per_item, int mutual)
+{
+    if (!w) {
+        set_error("fmm_multi_set_config: null handle");
+        return FMM_ERR_ARG;
+    }
+    if (targets_per_item != 0 && targets_per_item != 8 && targets_per_item != 16) {
+        set_error("fmm_multi_set_config: targets_per_item must be 0 (tune), 8 or 16");
+        return FMM_ERR_ARG;
+    }
+    if (mutual < -1 || mutual > 1) {
+        set_error("fmm_multi_set_config: mutual must be -1 (tune), 0 or 1");
+        return FMM_ERR_ARG;
+    }
+    w->m.pin_g = targets_per_item;
+    w->m.pin_mutual = mutual;
+    w->m.tuned = false;   // applied (and the table timed again) at the next evaluation
+    return FMM_OK;
+}
+
 int fmm_multi_info(fmm_multi *w, struct fmm_multi_info *info)
 {
     if (!w || !info) {
@@ -507,8 +587,8 @@ int fmm_multi_info(fmm_multi *w, struct fmm_multi_info *info)
     info->n_m2l = m.n_m2l;
     info->p2p_pairs = m.p2p_pairs;
     info->p2p_targets_per_item = m.hm.p2p_g ? m.hm.p2p_g : 16;
-    info->tune_ms[0] = m.tune_ms[0];
-    info->tune_ms[1] = m.tune_ms[1];
+    info->mutual = m.hm.mutual_ready ? 1 : 0;
+    for (int i = 0; i < 4; ++i) info->tune_ms[i] = m.tune_ms[i];
     info->graph_nodes = (int64_t)m.graph_nodes;
     info->kernel_launches = m.hm.launches;
     if (m.timed) {

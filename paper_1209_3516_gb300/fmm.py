@@ -59,8 +59,8 @@ class _MultiInfo(ctypes.Structure):
     _fields_ = [("n_total", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
                 ("n_m2l", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("nsys", ctypes.c_int32), ("nlevels", ctypes.c_int32),
-                ("p2p_targets_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double * 2), ("ms_evaluate", ctypes.c_double)]
+                ("p2p_targets_per_item", ctypes.c_int32), ("mutual", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * 4), ("ms_evaluate", ctypes.c_double)]
 
 
 _lib = None
@@ -106,6 +106,7 @@ def load():
     L.fmm_multi_info.argtypes = [_vp, ctypes.POINTER(_MultiInfo)]
     L.fmm_multi_destroy.argtypes = [_vp]
     L.fmm_multi_set_hybrid.argtypes = [_vp, ctypes.c_int64]
+    L.fmm_multi_set_config.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.fmm_set_hybrid.argtypes = [_vp, ctypes.c_int64]
     L.fmm_tune_hybrid.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_int, _vp, _vp,
                                   ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Options),
@@ -413,9 +414,13 @@ class MultiFMM:
                                          _dev_ptr(grad, torch.float32, (self.N, 3), "grad")))
         return phi, grad
 
+    def set_config(self, targets_per_item=0, mutual=-1):
+        """fmm_multi_set_config: pin the near field (0 / -1 let the autotuner choose)."""
+        _check(load().fmm_multi_set_config(self._h, int(targets_per_item), int(mutual)))
+
     def info(self) -> dict:
         i = _MultiInfo()
         _check(load().fmm_multi_info(self._h, ctypes.byref(i)))
         d = {k: getattr(i, k) for k, _ in _MultiInfo._fields_ if k not in ("tune_ms", "reserved")}
-        d["tune_ms"] = [i.tune_ms[0], i.tune_ms[1]]
+        d["tune_ms"] = [i.tune_ms[k] for k in range(4)]
         return d

@@ -107,6 +107,7 @@ def test_every_entry_point_rejects_null_arguments_before_any_device_call(lib):
         ("fmm_multi_evaluate", (V(), V(), V(), V())),
         ("fmm_multi_info", (V(), V())),
         ("fmm_multi_set_hybrid", (V(), ctypes.c_int64(0))),
+        ("fmm_multi_set_config", (V(), ctypes.c_int(0), ctypes.c_int(-1))),
     ]
     for name, args in calls:
         assert getattr(lib, name)(*args) == -1, name

@@ -52,10 +52,12 @@ def systems(sizes, seed, plummer_every=0):
     return xs, qs
 
 
-def run_multi(torch, xs, qs, P, theta, ncrit, hybrid=None):
+def run_multi(torch, xs, qs, P, theta, ncrit, hybrid=None, config=None):
     from paper_1209_3516_gb300 import fmm
     sizes = [x.shape[0] for x in xs]
     m = fmm.MultiFMM(sizes, P, theta, ncrit, hybrid=hybrid)
+    if config is not None:
+        m.set_config(*config)
     m.build(torch.from_numpy(np.concatenate(xs)).cuda())
     q = torch.from_numpy(np.concatenate(qs)).cuda()
     phi, grad = m.evaluate(q)
@@ -152,6 +154,26 @@ def test_multi_with_hybrid(torch_cuda):
         n = x.shape[0]
         pr, gr = oracle.FMM(n, 8, 0.5, 32, hybrid_min_pairs=0).build(x).evaluate(qq.astype(np.float64))
         assert rel_l2(phi[off:off + n], pr) <= TOL and rel_l2(grad[off:off + n], gr) <= TOL
+        assert peak_rel(phi[off:off + n], pr) <= 10 * TOL and peak_rel(grad[off:off + n], gr) <= 10 * TOL
+        off += n
+    m.close()
+
+
+@pytest.mark.parametrize("g,mutual", [(16, 0), (8, 0), (16, 1), (8, 1)])
+def test_multi_every_tile_configuration(torch_cuda, g, mutual):
+    # each configuration the autotuner may choose, pinned: every system against its oracle
+    sizes = [5000, 40, 11000, 900, 3001]
+    xs, qs = systems(sizes, 5400, plummer_every=2)
+    m, q, phi, grad = run_multi(torch_cuda, xs, qs, 6, 0.45, 32, config=(g, mutual))
+    info = m.info()
+    assert info["p2p_targets_per_item"] == g and info["mutual"] == mutual
+    assert all(t > 0 for t in info["tune_ms"])
+    phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+    off = 0
+    for x, qq in zip(xs, qs):
+        n = x.shape[0]
+        pr, gr = oracle.FMM(n, 6, 0.45, 32).build(x).evaluate(qq.astype(np.float64))
+        assert rel_l2(phi[off:off + n], pr) <= TOL and rel_l2(grad[off:off + n], gr) <= TOL, (n, g, mutual)
         assert peak_rel(phi[off:off + n], pr) <= 10 * TOL and peak_rel(grad[off:off + n], gr) <= 10 * TOL
         off += n
     m.close()
