@@ -97,11 +97,16 @@ def test_multi_graph_replay_and_recapture(torch_cuda):
     p1, g1 = phi1.clone(), grad1.clone()
     phi2, grad2 = m.evaluate(q, phi=phi1, grad=grad1)   # same pointers: graph replay
     torch.cuda.synchronize()
-    assert torch.equal(phi2, p1) and torch.equal(grad2, g1)
+    if m.info()["mutual"]:   # float reductions of the mutual near field: equal to rounding
+        assert rel_l2(phi2.cpu().numpy(), p1.cpu().numpy().astype(np.float64)) <= 1e-6
+        assert rel_l2(grad2.cpu().numpy(), g1.cpu().numpy().astype(np.float64)) <= 1e-6
+    else:                    # one-sided: bitwise the same
+        assert torch.equal(phi2, p1) and torch.equal(grad2, g1)
     q2 = q * 2.0                                       # new pointer: new capture, linear in q
     phi3, grad3 = m.evaluate(q2)
     torch.cuda.synchronize()
-    assert torch.allclose(phi3, 2 * p1, rtol=1e-6, atol=0) and torch.allclose(grad3, 2 * g1, rtol=1e-6, atol=0)
+    assert rel_l2(phi3.cpu().numpy(), 2 * p1.cpu().numpy().astype(np.float64)) <= 1e-6
+    assert rel_l2(grad3.cpu().numpy(), 2 * g1.cpu().numpy().astype(np.float64)) <= 1e-6
     # the same systems through plain handles agree to rounding
     from paper_1209_3516_gb300 import fmm
     off = 0
