@@ -146,6 +146,10 @@ constexpr int kMuG = 16;           // targets per work item (the P2P items)
 constexpr int kMuThreads = 64;     // two warps per block
 constexpr int kMuSlots = 256;      // staged sources per buffer
 constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots * (int)sizeof(float4));
+#ifndef FMM_MU_PER_LANE
+#define FMM_MU_PER_LANE 4
+#endif
+constexpr int kMuPerLane = FMM_MU_PER_LANE;   // staged sources per lane per step
 #ifndef FMM_MU_MIN_BLOCKS
 #define FMM_MU_MIN_BLOCKS 4
 #endif
@@ -185,39 +189,43 @@ __device__ __forceinline__ int mu_stage(RunCursor &cur, const float4 *run, const
     return slots;
 }
 
-// Both directions of the pair terms of one source (in the target frame, charge
-// sq) with NT targets, two per packed instruction: ntx.. negated target
+// Both directions of the pair terms of U sources (in the target frame, charges
+// in w) with NT targets, two per packed instruction: ntx.. negated target
 // positions, nqt negated target charges; acc[4h + k] the target side, ps, gs
-// the source's reaction (ps accumulates -phi_s).
-template <int NT>
-__device__ __forceinline__ void mu_tile(const float4 &s, const float2 *ntx, const float2 *nty, const float2 *ntz,
-                                        const float2 *nqt, float2 *acc, float2 &ps, float2 &gsx, float2 &gsy,
-                                        float2 &gsz)
+// the sources' reactions (ps accumulates -phi_s).
+template <int NT, int U>
+__device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx, const float2 *nty, const float2 *ntz,
+                                        const float2 *nqt, float2 *acc, float2 *ps, float2 *gsx, float2 *gsy,
+                                        float2 *gsz)
 {
     constexpr float kEps = 1.17549435e-38f;
-    const float2 sx = make_float2(s.x, s.x), sy = make_float2(s.y, s.y), sz = make_float2(s.z, s.z);
-    const float2 sq = make_float2(s.w, s.w);
     const float2 eps = make_float2(kEps, kEps);
 #pragma unroll
     for (int h = 0; h < NT / 2; ++h) {
-        const float2 dx = __fadd2_rn(sx, ntx[h]), dy = __fadd2_rn(sy, nty[h]), dz = __fadd2_rn(sz, ntz[h]);
-        float2 r2 = __ffma2_rn(dx, dx, eps);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-        const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
-        // target side: phi_t += q_s / r, grad_t += q_s e / r^3
-        acc[4 * h + 0] = __ffma2_rn(sq, rinv, acc[4 * h + 0]);
-        const float2 qs3 = __fmul2_rn(sq, rinv3);
-        acc[4 * h + 1] = __ffma2_rn(qs3, dx, acc[4 * h + 1]);
-        acc[4 * h + 2] = __ffma2_rn(qs3, dy, acc[4 * h + 2]);
-        acc[4 * h + 3] = __ffma2_rn(qs3, dz, acc[4 * h + 3]);
-        // reaction: -phi_s += (-q_t) / r, grad_s += (-q_t) e / r^3
-        ps = __ffma2_rn(nqt[h], rinv, ps);
-        const float2 qt3 = __fmul2_rn(nqt[h], rinv3);
-        gsx = __ffma2_rn(qt3, dx, gsx);
-        gsy = __ffma2_rn(qt3, dy, gsy);
-        gsz = __ffma2_rn(qt3, dz, gsz);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float2 sq = make_float2(s[u].w, s[u].w);
+            const float2 dx = __fadd2_rn(make_float2(s[u].x, s[u].x), ntx[h]);
+            const float2 dy = __fadd2_rn(make_float2(s[u].y, s[u].y), nty[h]);
+            const float2 dz = __fadd2_rn(make_float2(s[u].z, s[u].z), ntz[h]);
+            float2 r2 = __ffma2_rn(dx, dx, eps);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const float2 rinv3 = __fmul2_rn(__fmul2_rn(rinv, rinv), rinv);
+            // target side: phi_t += q_s / r, grad_t += q_s e / r^3
+            acc[4 * h + 0] = __ffma2_rn(sq, rinv, acc[4 * h + 0]);
+            const float2 qs3 = __fmul2_rn(sq, rinv3);
+            acc[4 * h + 1] = __ffma2_rn(qs3, dx, acc[4 * h + 1]);
+            acc[4 * h + 2] = __ffma2_rn(qs3, dy, acc[4 * h + 2]);
+            acc[4 * h + 3] = __ffma2_rn(qs3, dz, acc[4 * h + 3]);
+            // reaction: -phi_s += (-q_t) / r, grad_s += (-q_t) e / r^3
+            ps[u] = __ffma2_rn(nqt[h], rinv, ps[u]);
+            const float2 qt3 = __fmul2_rn(nqt[h], rinv3);
+            gsx[u] = __ffma2_rn(qt3, dx, gsx[u]);
+            gsy[u] = __ffma2_rn(qt3, dy, gsy[u]);
+            gsz[u] = __ffma2_rn(qt3, dz, gsz[u]);
+        }
     }
 }
 
@@ -237,21 +245,33 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
         cp_async_commit();
         cp_async_wait_1();
         __syncwarp();
-        for (int t0 = 0; t0 < n_cur; t0 += 32) {
-            const int j = t0 + lane;
-            float4 s = make_float4(1e20f, 1e20f, 1e20f, 0.f);   // past the count: far away, no charge
-            int sidx = -1;
-            if (j < n_cur) {
-                s = cur_part[j];
-                const float4 d = cur_shift[j];
-                s.x += d.x;
-                s.y += d.y;
-                s.z += d.z;
-                sidx = __float_as_int(d.w);
+#pragma unroll 1
+        for (int t0 = 0; t0 < n_cur; t0 += 32 * kMuPerLane) {
+            // kMuPerLane staged sources per lane per step: independent chains side by side
+            float4 s[kMuPerLane];
+            int sidx[kMuPerLane];
+            float2 ps[kMuPerLane], gsx[kMuPerLane], gsy[kMuPerLane], gsz[kMuPerLane];
+#pragma unroll
+            for (int u = 0; u < kMuPerLane; ++u) {
+                const int j = t0 + 32 * u + lane;
+                s[u] = make_float4(1e20f, 1e20f, 1e20f, 0.f);   // past the count: far away, no charge
+                sidx[u] = -1;
+                if (j < n_cur) {
+                    s[u] = cur_part[j];
+                    const float4 d = cur_shift[j];
+                    s[u].x += d.x;
+                    s[u].y += d.y;
+                    s[u].z += d.z;
+                    sidx[u] = __float_as_int(d.w);
+                }
+                ps[u] = gsx[u] = gsy[u] = gsz[u] = make_float2(0.f, 0.f);
             }
-            float2 ps = make_float2(0.f, 0.f), gsx = ps, gsy = ps, gsz = ps;
-            mu_tile<NT>(s, ntx, nty, ntz, nqt, acc, ps, gsx, gsy, gsz);
-            if (sidx >= 0) red_add_v4(racc + sidx, -(ps.x + ps.y), gsx.x + gsx.y, gsy.x + gsy.y, gsz.x + gsz.y);
+            mu_tile<NT, kMuPerLane>(s, ntx, nty, ntz, nqt, acc, ps, gsx, gsy, gsz);
+#pragma unroll
+            for (int u = 0; u < kMuPerLane; ++u)
+                if (sidx[u] >= 0)
+                    red_add_v4(racc + sidx[u], -(ps[u].x + ps[u].y), gsx[u].x + gsx[u].y, gsy[u].x + gsy[u].y,
+                               gsz[u].x + gsz[u].y);
         }
         __syncwarp();   // every lane is done with this buffer before it is refilled
         n_cur = n_next;
