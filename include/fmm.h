@@ -71,6 +71,7 @@ enum {
     FMM_PHASE_TREE,        /* ncrit splitting, cell table, cell geometry */
     FMM_PHASE_TRAVERSE,    /* dual tree traversal (seeding rounds + work-stack kernel) */
     FMM_PHASE_LISTS,       /* grouping of the lists by target cell */
+    FMM_PHASE_ITEMS,       /* P2P source runs, the mutual schedule's list split, work items */
     FMM_PHASE_UPWARD,      /* charge gather, P2M, M2M */
     FMM_PHASE_M2L,
     FMM_PHASE_DOWNWARD,    /* L2L */

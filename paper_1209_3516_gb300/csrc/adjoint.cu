@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
 
 template <int P> static int adjoint_p2p_impl(Handle &h, float *dq, float *dx)
 {
+    FMM_TRY(ensure_full_runs(h));
     static bool configured[64] = {};
     if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
         FMM_CUDA(cudaFuncSetAttribute(k_p2p_adj<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem));

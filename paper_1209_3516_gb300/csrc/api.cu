@@ -123,7 +123,9 @@ static int do_build(Handle &h, const double *x)
     FMM_TRY(build_keys(h, x));
     FMM_TRY(build_tree(h, x));
     FMM_TRY(build_lists(h));
+    phase_begin(h, FMM_PHASE_ITEMS);
     FMM_TRY(build_p2p_items(h));
+    phase_end(h, FMM_PHASE_ITEMS);
     if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
     FMM_CUDA(cudaStreamSynchronize(h.stream));
     if (h.events_ready) cudaEventElapsedTime(&h.ms_build, h.ev[ev0], h.ev[ev1]);

@@ -700,6 +700,7 @@ template <int P> static int p2p_batch_tc_impl(Handle &h, int nrhs, float *phi, f
 {
     constexpr int T = MI<P>::T;
     const int nl = (int)h.nleaves;
+    FMM_TRY(ensure_full_runs(h));
     if (!h.tc_items_ready) {
         FMM_TRY(build_work_items(h, kTcTargets, h.tc_items, h.n_tc_items));
         h.tc_items_ready = true;

@@ -152,7 +152,7 @@ struct Handle {
     // (B > A, mirrored) and one-sided ones (CSR by cell), their source runs, and
     // the accumulator of the mutual pass (float4 per sorted particle)
     bool mutual_ready = false;
-    int64_t n_mutual = 0, n_onesided = 0, n_mu_runs = 0, n_os_runs = 0;
+    bool full_runs_ready = false;   // the whole lists' runs (p2p_poff / ent / cnt) are built
     DevBuf mu_off, mu_src, os_off, os_src, mu_cnt_tmp;
     DevBuf mu_poff, mu_ent, mu_cnt, os_poff, os_ent, os_cnt;
     DevBuf racc;
@@ -213,7 +213,9 @@ int build_lists(Handle &h);                       // DTT + grouping
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
 int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items);   // items of <= g targets
 int p2p_batch_tc(Handle &h, int nrhs, float *phi, float *grad);   // batched P2P + L2P, tensor cores
-int build_runs(Handle &h, const int *off, const int *src, DevBuf &roff, DevBuf &ent, DevBuf &cnt, int64_t &nruns);
+int build_runs(Handle &h, const int *off, const int *src, int64_t max_runs, DevBuf &roff, DevBuf &ent, DevBuf &cnt,
+               int64_t *nruns);
+int ensure_full_runs(Handle &h);   // the whole lists' runs (built on first use with the mutual schedule)
 int build_mutual(Handle &h);   // split the P2P lists for the mutual schedule
 int p2p_mutual(Handle &h);     // the mutual P2P pass (fills racc)
 

@@ -263,6 +263,7 @@ static int merge_systems(Multi &m)
     hm.p2p_g = 0;
     FMM_TRY(build_work_items(hm, 16, hm.p2p_items, hm.n_items));
     hm.built = true;
+    hm.full_runs_ready = true;   // the merged runs
     m.merged = true;
     m.tuned = false;
     if (m.exec) {

@@ -120,20 +120,15 @@ int build_mutual(Handle &h)
     unsigned *mo = h.mu_off.as<unsigned>(), *oo = h.os_off.as<unsigned>();
     FMM_TRY(scan_exclusive_u32(h, cm, mo, nc, mo + nc));
     FMM_TRY(scan_exclusive_u32(h, co, oo, nc, oo + nc));
-    unsigned tot[2];
-    FMM_CUDA(cudaMemcpyAsync(&tot[0], mo + nc, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
-    FMM_CUDA(cudaMemcpyAsync(&tot[1], oo + nc, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
-    FMM_CUDA(cudaStreamSynchronize(h.stream));
-    h.n_mutual = tot[0];
-    h.n_onesided = tot[1];
-    FMM_TRY(h.mu_src.reserve(std::max<size_t>(tot[0], 1) * sizeof(int)));
-    FMM_TRY(h.os_src.reserve(std::max<size_t>(tot[1], 1) * sizeof(int)));
+    // both parts are sized for the whole list (no count read back)
+    FMM_TRY(h.mu_src.reserve(std::max<int64_t>(h.n_p2p, 1) * sizeof(int)));
+    FMM_TRY(h.os_src.reserve(std::max<int64_t>(h.n_p2p, 1) * sizeof(int)));
     ++h.launches;
     k_mutual_write<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
                                                  kind, mo, oo, h.mu_src.as<int>(), h.os_src.as<int>());
     FMM_CHECK_LAUNCH("mutual list split");
-    FMM_TRY(build_runs(h, h.mu_off.as<int>(), h.mu_src.as<int>(), h.mu_poff, h.mu_ent, h.mu_cnt, h.n_mu_runs));
-    FMM_TRY(build_runs(h, h.os_off.as<int>(), h.os_src.as<int>(), h.os_poff, h.os_ent, h.os_cnt, h.n_os_runs));
+    FMM_TRY(build_runs(h, h.mu_off.as<int>(), h.mu_src.as<int>(), h.n_p2p, h.mu_poff, h.mu_ent, h.mu_cnt, nullptr));
+    FMM_TRY(build_runs(h, h.os_off.as<int>(), h.os_src.as<int>(), h.n_p2p, h.os_poff, h.os_ent, h.os_cnt, nullptr));
     FMM_TRY(h.racc.reserve((size_t)h.N * sizeof(float4)));
     h.mutual_ready = true;
     return FMM_OK;

@@ -465,9 +465,12 @@ int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items)
 }
 
 // Source runs of the lists (off, src) of every leaf: run offsets per leaf-list
-// entry (roff, nleaves + 1), run records and end particles; *nruns their count.
-int build_runs(Handle &h, const int *off, const int *src, DevBuf &roff_buf, DevBuf &ent, DevBuf &cnt,
-               int64_t &nruns)
+// entry (roff, nleaves + 1), run records and end particles.  The buffers are
+// sized for max_runs (a run starts at a list entry, so the list's length
+// bounds it) without reading the count back; with nruns the count is read
+// back too (one host round trip).
+int build_runs(Handle &h, const int *off, const int *src, int64_t max_runs, DevBuf &roff_buf, DevBuf &ent,
+               DevBuf &cnt, int64_t *nruns)
 {
     const int nl = (int)h.nleaves;
     FMM_TRY(h.c_tmp.reserve((size_t)(nl + 1) * sizeof(unsigned)));
@@ -478,26 +481,41 @@ int build_runs(Handle &h, const int *off, const int *src, DevBuf &roff_buf, DevB
     k_p2p_run_count<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
         nl, h.leaf_list.as<int>(), off, src, h.c_parent.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(), nrun);
     FMM_TRY(scan_exclusive_u32(h, nrun, roff, nl, roff + nl));
-    FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, roff + nl, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
-    FMM_CUDA(cudaStreamSynchronize(h.stream));
-    nruns = h.pinned->level_total;
-    FMM_TRY(ent.reserve(std::max<int64_t>(nruns, 1) * sizeof(float4)));
-    FMM_TRY(cnt.reserve(std::max<int64_t>(nruns, 1) * sizeof(int)));
+    FMM_TRY(ent.reserve(std::max<int64_t>(max_runs, 1) * sizeof(float4)));
+    FMM_TRY(cnt.reserve(std::max<int64_t>(max_runs, 1) * sizeof(int)));
     ++h.launches;
     k_p2p_runs<<<ceil_div((int64_t)nl * 32, 256), 256, 0, h.stream>>>(
         nl, h.leaf_list.as<int>(), off, src, h.c_parent.as<int>(), h.c_pbeg.as<int>(), h.c_pcnt.as<int>(),
         h.c_geom.as<float4>(), roff, ent.as<float4>(), cnt.as<int>());
     FMM_CHECK_LAUNCH("p2p runs");
+    if (nruns) {
+        FMM_CUDA(cudaMemcpyAsync(&h.pinned->level_total, roff + nl, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 h.stream));
+        FMM_CUDA(cudaStreamSynchronize(h.stream));
+        *nruns = h.pinned->level_total;
+    }
+    return FMM_OK;
+}
+
+// The runs of the full lists (one-sided near field, adjoint, batched forms);
+// with the mutual schedule they are built on first use.
+int ensure_full_runs(Handle &h)
+{
+    if (h.full_runs_ready) return FMM_OK;
+    FMM_TRY(build_runs(h, h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.n_p2p, h.p2p_poff, h.p2p_ent, h.p2p_cnt,
+                       &h.n_pieces));
+    h.full_runs_ready = true;
     return FMM_OK;
 }
 
 int build_p2p_items(Handle &h)
 {
-    // source runs of every target leaf's list
-    FMM_TRY(build_runs(h, h.p2p_off.as<int>(), h.p2p_src.as<int>(), h.p2p_poff, h.p2p_ent, h.p2p_cnt, h.n_pieces));
-    // the mutual schedule's split of the lists
+    // the mutual schedule's split of the lists, or the source runs of every
+    // target leaf's whole list
     h.mutual_ready = false;
+    h.full_runs_ready = false;
     if (h.flags & FMM_FLAG_MUTUAL) FMM_TRY(build_mutual(h));
+    else FMM_TRY(ensure_full_runs(h));
     // work items (the adjoint's items are built on first use)
     h.adj_items_ready = false;
     h.tc_items_ready = false;

@@ -25,7 +25,7 @@ FMM_FLAG_KAHAN = 1
 FMM_FLAG_TIMING = 2
 FMM_FLAG_MUTUAL = 4
 
-PHASES = ["morton", "sort", "tree", "traverse", "lists", "upward", "m2l", "downward", "p2p"]
+PHASES = ["morton", "sort", "tree", "traverse", "lists", "items", "upward", "m2l", "downward", "p2p"]
 
 
 class FMMError(RuntimeError):
