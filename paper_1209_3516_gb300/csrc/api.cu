@@ -235,7 +235,7 @@ int fmm_destroy(fmm_handle *w)
                       &h.adj, &h.Ma, &h.La, &h.adj_items, &h.qb, &h.qbh, &h.qbl, &h.Mb, &h.Lb,
                       &h.c_scale, &h.tc_items, &h.lbh, &h.lbl, &h.tc_next, &h.mu_off, &h.mu_src,
                       &h.os_off, &h.os_src, &h.mu_cnt_tmp, &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent,
-                      &h.os_cnt, &h.racc};
+                      &h.os_cnt, &h.racc, &h.Mf};
     for (DevBuf *b : bufs) b->release();
     if (h.events_ready)
         for (auto &ev : h.ev) cudaEventDestroy(ev);

@@ -140,22 +140,57 @@ __global__ void k_m2m_batch(int lo, int n, const int *cbeg, const int *ccnt, con
     for (int t = 0; t < TP; ++t) dst[t * kB] = t < T ? acc[t] : 0.0f;
 }
 
-// M2L: one warp per target cell; per chunk of 32 sources each lane computes the
-// kernel derivatives of one pair into shared memory, then lane r contracts
-// every pair of the chunk with its multipole vector r.
-constexpr int kM2LBatchThreads = 64;   // two warps: 2 x 32 x (T + 1) floats of D fit static shared memory
+// M2L in the harmonic reduction of the single-vector M2L (mi.cuh, HI): the
+// multipoles are first folded in place onto their components with k_z <= 1
+// (rows fidx(k) of each cell, lane = vector), then one warp per target cell
+// computes, per chunk of 32 sources, the derivatives D_m (m_z <= 2) of one
+// pair per lane into shared memory, and lane r contracts every pair of the
+// chunk with its folded multipole vector r into the outputs n_z <= 1; the
+// outputs n_z >= 2 follow from the trace identity in the epilogue.
+constexpr int kM2LBatchThreads = 64;
 
-// Outputs N0 <= idx(n) < N1 only (at P = 8 two launches split them, as for the
-// single-vector M2L: half the accumulators, no spills; multipole coefficients
-// that no output of the slice uses are not loaded).
-template <int P, int N0, int N1>
+// Mb[c][fidx(k)][r] <- folded multipole of vector r (in place: rows 0 .. F-1).
+template <int P>
+__global__ void k_m2l_fold_batch(int ncells, float *Mb)
+{
+    constexpr int T = MI<P>::T, TP = MI<P>::TP;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= ncells) return;
+    float *cm = Mb + (size_t)c * TP * kB + lane_id();
+    float m[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) m[i] = cm[i * kB];
+#pragma unroll
+    for (int z = P - 1; z >= 2; --z)
+#pragma unroll
+        for (int n = z; n < P; ++n)
+#pragma unroll
+            for (int a = n - z; a >= 0; --a) {
+                const int b = n - z - a;
+                const float v = m[MI<P>::idx(a, b, z)];
+                m[MI<P>::idx(a + 2, b, z - 2)] -= v;
+                m[MI<P>::idx(a, b + 2, z - 2)] -= v;
+            }
+#pragma unroll
+    for (int e = 0; e < P; ++e)
+#pragma unroll
+        for (int kc = 0; kc <= 1; ++kc)
+#pragma unroll
+            for (int a = e - kc; a >= 0; --a) {
+                if (kc > e) continue;
+                const int b = e - kc - a;
+                cm[HI<P>::fidx(a, b, kc) * kB] = m[MI<P>::idx(a, b, kc)];
+            }
+}
+
+template <int P>
 __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, const int *off, const int *src,
                                                                 const int *level, const float4 *geom, const float *Mb,
                                                                 float *Lb)
 {
-    constexpr int T = MI<P>::T, TP = MI<P>::TP, NO = N1 - N0;
+    constexpr int T = MI<P>::T, TP = MI<P>::TP, F = HI<P>::F, ND = HI<P>::ND;
     constexpr int W = kM2LBatchThreads / 32;
-    __shared__ float Ds[W][32][T + 1];
+    __shared__ float Ds[W][32][ND + 1];
     __shared__ float Rho[W][32];
     __shared__ int Src[W][32];
     const int w = threadIdx.x >> 5;
@@ -165,19 +200,19 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
     const float4 Xt = geom[t];
     const int lt = level[t];
     const float inv_st = ldexpf(1.0f, lt);
-    float acc[NO];
+    float acc[F];
 #pragma unroll
-    for (int i = 0; i < NO; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < F; ++i) acc[i] = 0.0f;
     const int b = off[t], e = off[t + 1];
     for (int k0 = b; k0 < e; k0 += 32) {
         const int k = k0 + lane;
         if (k < e) {
             const int s = src[k];
             const float4 Xs = geom[s];
-            float D[T];
-            laplace_derivatives<P>((Xt.x - Xs.x) * inv_st, (Xt.y - Xs.y) * inv_st, (Xt.z - Xs.z) * inv_st, D);
+            float D[ND];
+            laplace_derivatives_z2<P>((Xt.x - Xs.x) * inv_st, (Xt.y - Xs.y) * inv_st, (Xt.z - Xs.z) * inv_st, D);
 #pragma unroll
-            for (int i = 0; i < T; ++i) Ds[w][lane][i] = D[i];
+            for (int i = 0; i < ND; ++i) Ds[w][lane][i] = D[i];
             Rho[w][lane] = ldexpf(1.0f, lt - level[s]);
             Src[w][lane] = s;
         }
@@ -189,25 +224,24 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
             const float rho = Rho[w][j];
             float rp = 1.0f;
 #pragma unroll
-            for (int nk = 0; nk < P; ++nk) {
+            for (int ke = 0; ke < P; ++ke) {
 #pragma unroll
-                for (int ka = nk; ka >= 0; --ka)
+                for (int kc = 0; kc <= 1; ++kc)
 #pragma unroll
-                    for (int kb = nk - ka; kb >= 0; --kb) {
-                        const int kc = nk - ka - kb;
-                        // the outputs of this slice that k reaches: degrees 0 .. P-1-nk
-                        if (N0 >= MI<P>::idx(P - nk, 0, 0)) continue;
-                        const float m = Mj[MI<P>::idx(ka, kb, kc) * kB] * rp;
+                    for (int ka = ke - kc; ka >= 0; --ka) {
+                        if (kc > ke) continue;
+                        const int kb = ke - kc - ka;
+                        const float m = Mj[HI<P>::fidx(ka, kb, kc) * kB] * rp;
 #pragma unroll
-                        for (int nn = 0; nn + nk < P; ++nn)
+                        for (int d = 0; d + ke < P; ++d)
 #pragma unroll
-                            for (int na = nn; na >= 0; --na)
+                            for (int nc = 0; nc <= 1; ++nc)
 #pragma unroll
-                                for (int nb = nn - na; nb >= 0; --nb) {
-                                    const int nc = nn - na - nb;
-                                    const int in = MI<P>::idx(na, nb, nc);
-                                    if (in >= N0 && in < N1)
-                                        acc[in - N0] = fmaf(m, D[MI<P>::idx(na + ka, nb + kb, nc + kc)], acc[in - N0]);
+                                for (int na = d - nc; na >= 0; --na) {
+                                    if (nc > d) continue;
+                                    const int nb = d - nc - na;
+                                    const int in = HI<P>::fidx(na, nb, nc);
+                                    acc[in] = fmaf(m, D[HI<P>::didx(na + ka, nb + kb, nc + kc)], acc[in]);
                                 }
                     }
                 rp *= rho;
@@ -215,12 +249,29 @@ __global__ void __launch_bounds__(kM2LBatchThreads) k_m2l_batch(int ncells, cons
         }
         __syncwarp();
     }
+    float full[T];
+#pragma unroll
+    for (int d = 0; d < P; ++d)
+#pragma unroll
+        for (int nc = 0; nc <= 1; ++nc)
+#pragma unroll
+            for (int na = d - nc; na >= 0; --na) {
+                if (nc > d) continue;
+                const int nb = d - nc - na;
+                full[MI<P>::idx(na, nb, nc)] = acc[HI<P>::fidx(na, nb, nc)] * inv_st;
+            }
+#pragma unroll
+    for (int z = 2; z < P; ++z)
+#pragma unroll
+        for (int d = z; d < P; ++d)
+#pragma unroll
+            for (int na = d - z; na >= 0; --na) {
+                const int nb = d - z - na;
+                full[MI<P>::idx(na, nb, z)] = -full[MI<P>::idx(na + 2, nb, z - 2)] - full[MI<P>::idx(na, nb + 2, z - 2)];
+            }
     float *dst = Lb + (size_t)t * TP * kB + lane;
 #pragma unroll
-    for (int i = 0; i < NO; ++i) dst[(N0 + i) * kB] = acc[i] * inv_st;
-    if (N1 == T)
-#pragma unroll
-        for (int i = T; i < TP; ++i) dst[i * kB] = 0.0f;
+    for (int i = 0; i < TP; ++i) dst[i * kB] = i < T ? full[i] : 0.0f;
 }
 
 template <int P>
@@ -293,18 +344,10 @@ template <int P> static int batch_impl(Handle &h, const float *q, int nrhs, floa
     phase_end(h, FMM_PHASE_UPWARD);
     phase_begin(h, FMM_PHASE_M2L);
     ++h.launches;
-    {
-        constexpr int T = MI<P>::T;
-        constexpr int H = P >= 8 ? ((T / 2 + 3) & ~3) : T;   // two launches at P = 8
-        const int mb = ceil_div((int64_t)nc * 32, kM2LBatchThreads);
-        k_m2l_batch<P, 0, H><<<mb, kM2LBatchThreads, 0, h.stream>>>(
-            nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
-        if constexpr (H < T) {
-            ++h.launches;
-            k_m2l_batch<P, H, T><<<mb, kM2LBatchThreads, 0, h.stream>>>(
-                nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
-        }
-    }
+    k_m2l_fold_batch<P><<<ceil_div((int64_t)nc * 32, 128), 128, 0, h.stream>>>(nc, Mb);
+    ++h.launches;
+    k_m2l_batch<P><<<ceil_div((int64_t)nc * 32, kM2LBatchThreads), kM2LBatchThreads, 0, h.stream>>>(
+        nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), Mb, Lb);
     phase_end(h, FMM_PHASE_M2L);
     phase_begin(h, FMM_PHASE_DOWNWARD);
     for (int l = 1; l < h.nlevels; ++l) {

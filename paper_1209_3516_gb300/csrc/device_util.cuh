@@ -78,4 +78,14 @@ __device__ __forceinline__ void warp_append(bool pred, const T &val, T *buf, uns
     }
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L1 and L2),
+// grouped by commit; wait_group 1 leaves the most recent group in flight.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 }  // namespace fmm

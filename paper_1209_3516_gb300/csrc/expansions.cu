@@ -249,68 +249,153 @@ __global__ void __launch_bounds__(kM2MThreads) k_m2m_sep(int lo, const int *cbeg
 }
 
 // ---------------------------------------------------------------------------
-// M2L: Lb_n(T) = (1/s_T) sum_S sum_k (s_S/s_T)^|k| Mb_k(S) D_{n+k}((X_T - X_S)/s_T)
-// One warp per target cell, lanes over its M2L sources; each lane computes the
-// kernel derivatives of its pair and contracts them with the source multipole
-// (streamed from memory as float4) into the output coefficients
-// N0 <= idx(n) < N1, then the warp sums its lanes.  At P = 8 the outputs are
-// split over two launches of this pass (each recomputing D): one kernel with
-// the whole unrolled contraction stalls on instruction-cache misses (0.76 ms
-// at N = 1M, theta = 0.5), two passes in one kernel are worse (1.26 ms: both
-// bodies compete for the cache), two launches of half the body each take
-// 0.65 ms in total, three or more launches lose to the repeated D (0.82+ ms).
+// M2L: Lb_n(T) = (1/s_T) sum_S sum_k (s_S/s_T)^|k| Mb_k(S) D_{n+k}((X_T - X_S)/s_T),
+// evaluated in its harmonic reduction (mi.cuh, HI): every multipole is folded
+// once onto its k_z <= 1 components (k_m2l_fold); then one warp per target
+// cell, lanes over its M2L sources: each lane computes the derivatives D_m,
+// m_z <= 2, of its pair and contracts them with the folded multipole into the
+// outputs n_z <= 1; the warp sums its lanes, restores the outputs n_z >= 2
+// from the trace identity and writes all T coefficients.  Each lane streams
+// its sources' folded rows into a two-stage shared-memory ring with cp.async,
+// one chunk of 32 pairs ahead of the contraction.  The two-slice form of the
+// full contraction this replaces took 0.65 ms at N = 1M, P = 8, theta = 0.5.
 // ---------------------------------------------------------------------------
-template <int P, int N0, int N1>
-__device__ __forceinline__ void m2l_pass(int t, const int *off, const int *src, const int *level, const float4 *geom,
-                                         const float *M, float *L)
+template <int P> struct HarmLayout {
+    static constexpr int F = HI<P>::F;
+    static constexpr int Q = (F + 3) / 4;      // float4 of folded coefficients per row
+    static constexpr int G4 = Q + 1;           // + (centre, level): one row of Mf, in float4
+    static constexpr int FP = 4 * G4;          // row stride of Mf in floats
+    static constexpr int R4 = G4 | 1;          // row stride in the ring (odd: lanes' rows in distinct banks)
+    static constexpr int kWarps = 4;           // warps (target cells) per block of k_m2l
+    static constexpr size_t ring_bytes = (size_t)kWarps * 2 * 32 * R4 * sizeof(float4);
+};
+
+// Mf[c] = the multipole of cell c folded onto its components k_z <= 1 by the
+// trace identity (from the highest k_z down, each M_k with k_z >= 2 is
+// subtracted from M_{k-2e_z+2e_x} and M_{k-2e_z+2e_y}), at fidx(k), then the
+// cell's centre and level (as a float) in the row's last float4.
+template <int P>
+__global__ void k_m2l_fold(int ncells, const float *M, const float4 *geom, const int *level, float *Mf)
 {
-    constexpr int T = MI<P>::T, TP = MI<P>::TP, NO = N1 - N0;
+    constexpr int T = MI<P>::T, TP = MI<P>::TP, F = HI<P>::F, FP = HarmLayout<P>::FP;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    float m[T];
+    const float *src = M + (size_t)c * TP;
+#pragma unroll
+    for (int i = 0; i < T; ++i) m[i] = src[i];
+#pragma unroll
+    for (int z = P - 1; z >= 2; --z)
+#pragma unroll
+        for (int n = z; n < P; ++n)
+#pragma unroll
+            for (int a = n - z; a >= 0; --a) {
+                const int b = n - z - a;
+                const float v = m[MI<P>::idx(a, b, z)];
+                m[MI<P>::idx(a + 2, b, z - 2)] -= v;
+                m[MI<P>::idx(a, b + 2, z - 2)] -= v;
+            }
+    float *dst = Mf + (size_t)c * FP;
+#pragma unroll
+    for (int e = 0; e < P; ++e)
+#pragma unroll
+        for (int cc = 0; cc <= 1; ++cc)
+#pragma unroll
+            for (int a = e - cc; a >= 0; --a) {
+                if (cc > e) continue;
+                const int b = e - cc - a;
+                dst[HI<P>::fidx(a, b, cc)] = m[MI<P>::idx(a, b, cc)];
+            }
+#pragma unroll
+    for (int i = F; i < 4 * HarmLayout<P>::Q; ++i) dst[i] = 0.0f;
+    const float4 X = geom[c];
+    reinterpret_cast<float4 *>(dst)[HarmLayout<P>::Q] = make_float4(X.x, X.y, X.z, (float)level[c]);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 3) k_m2l(int ncells, const int *off, const int *src, const int *level,
+                                                const float4 *geom, const float4 *Mf, float *L)
+{
+    constexpr int T = MI<P>::T, TP = MI<P>::TP, F = HI<P>::F, ND = HI<P>::ND;
+    constexpr int Q = HarmLayout<P>::Q, G4 = HarmLayout<P>::G4, R4 = HarmLayout<P>::R4;
+    extern __shared__ float4 m2l_ring[];   // [warp][stage][lane][R4]
+    __shared__ float sums[HarmLayout<P>::kWarps][HarmLayout<P>::FP];   // the reduced outputs n_z <= 1
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= ncells) return;
+    const int lane = (int)lane_id();
+    const int w = (threadIdx.x >> 5) % HarmLayout<P>::kWarps;
+    float4 *row0 = m2l_ring + ((size_t)w * 2 * 32 + lane) * R4;   // stage 1 at + 32 R4
     const float4 Xt = geom[t];
     const int lt = level[t];
     const float inv_st = ldexpf(1.0f, lt);
-    float acc[ScatterLen<NO>::value];
+    float acc[ScatterLen<F>::value];
 #pragma unroll
-    for (int i = 0; i < ScatterLen<NO>::value; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < ScatterLen<F>::value; ++i) acc[i] = 0.0f;
     const int b = off[t], e = off[t + 1];
-    for (int k = b + (int)lane_id(); k < e; k += 32) {
-        const int s = src[k];
-        const float4 Xs = geom[s];
-        float D[T];
-        laplace_derivatives<P>((Xt.x - Xs.x) * inv_st, (Xt.y - Xs.y) * inv_st, (Xt.z - Xs.z) * inv_st, D);
-        const float rho = ldexpf(1.0f, lt - level[s]);   // s_S / s_T
-        float rho_pow[P];
-        rho_pow[0] = 1.0f;
+    // lane-private pipeline: the rows of entries b + lane + 32 i, one chunk ahead
+    int s = b + lane < e ? src[b + lane] : -1;
+    if (s >= 0)
 #pragma unroll
-        for (int d = 1; d < P; ++d) rho_pow[d] = rho_pow[d - 1] * rho;
-        m2l_contract_range<P, N0, N1>(reinterpret_cast<const float4 *>(M + (size_t)s * TP), rho_pow, D, acc);
-    }
-    float *dst = L + (size_t)t * TP;
-    const int lane = (int)lane_id();
-    if constexpr (NO <= 64) {
-        constexpr int K = Pad32Pow2<NO>::value / 32;
-        warp_reduce_scatter<NO>(acc);
+        for (int q = 0; q < G4; ++q) cp_async16(row0 + q, Mf + (size_t)s * G4 + q);
+    cp_async_commit();
+    int sn = b + 32 + lane < e ? src[b + 32 + lane] : -1;
+    int stage = 0;
+    for (int k0 = b; k0 < e; k0 += 32) {
+        float4 *nrow = row0 + (stage ^ 1) * 32 * R4;
+        if (sn >= 0)
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int i = K * lane + j;
-            if (i < NO) dst[N0 + i] = acc[j] * inv_st;
+            for (int q = 0; q < G4; ++q) cp_async16(nrow + q, Mf + (size_t)sn * G4 + q);
+        cp_async_commit();
+        const int snn = k0 + 64 + lane < e ? src[k0 + 64 + lane] : -1;
+        if (s >= 0) {
+            cp_async_wait_1();
+            const float4 *row = row0 + stage * 32 * R4;
+            const float4 Xs = row[Q];
+            float D[ND];
+            laplace_derivatives_z2<P>((Xt.x - Xs.x) * inv_st, (Xt.y - Xs.y) * inv_st, (Xt.z - Xs.z) * inv_st, D);
+            const float rho = ldexpf(1.0f, lt - (int)Xs.w);   // s_S / s_T
+            float rho_pow[P];
+            rho_pow[0] = 1.0f;
+#pragma unroll
+            for (int d = 1; d < P; ++d) rho_pow[d] = rho_pow[d - 1] * rho;
+            m2l_contract_harmonic<P>(row, rho_pow, D, acc);
         }
-    } else {
-        warp_reduce_vec<NO>(acc);
-#pragma unroll
-        for (int i = 0; i < NO; ++i)
-            if ((i & 31) == lane) dst[N0 + i] = acc[i] * inv_st;
+        s = sn;
+        sn = snn;
+        stage ^= 1;
     }
-    if (N1 == T)
-        for (int i = T + lane; i < TP; i += 32) dst[i] = 0.0f;
-}
-
-template <int P, int N0, int N1>
-__global__ void __launch_bounds__(128) k_m2l(int ncells, const int *off, const int *src, const int *level,
-                                             const float4 *geom, const float *M, float *L)
-{
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= ncells) return;
-    m2l_pass<P, N0, N1>(t, off, src, level, geom, M, L);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    warp_reduce_scatter<F>(acc);
+    float *sw = sums[w];
+    constexpr int K = Pad32Pow2<F>::value / 32;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int i = K * lane + j;
+        if (i < F) sw[i] = acc[j];
+    }
+    __syncwarp();
+    // every lane: all T outputs, n_z >= 2 from the trace identity, then its share written
+    float full[T];
+#pragma unroll
+    for (int d = 0; d < P; ++d)
+#pragma unroll
+        for (int cc = 0; cc <= 1; ++cc)
+#pragma unroll
+            for (int a = d - cc; a >= 0; --a) {
+                if (cc > d) continue;
+                const int bb = d - cc - a;
+                full[MI<P>::idx(a, bb, cc)] = sw[HI<P>::fidx(a, bb, cc)] * inv_st;
+            }
+#pragma unroll
+    for (int z = 2; z < P; ++z)
+#pragma unroll
+        for (int d = z; d < P; ++d)
+#pragma unroll
+            for (int a = d - z; a >= 0; --a) {
+                const int bb = d - z - a;
+                full[MI<P>::idx(a, bb, z)] = -full[MI<P>::idx(a + 2, bb, z - 2)] - full[MI<P>::idx(a, bb + 2, z - 2)];
+            }
+    warp_store_vec<T, TP>(full, L + (size_t)t * TP);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,35 +504,23 @@ template <int P> static int adjoint_upward_impl(Handle &h, const float *dphi, co
     return m2m_levels<P>(h, h.Ma.as<float>());
 }
 
-#ifndef FMM_M2L_KERNELS
-#define FMM_M2L_KERNELS 2
-#endif
-
-template <int P, int S, int I> struct M2LSlice {   // outputs [lo, hi) of launch I of S, multiples of 4
-    static constexpr int T = MI<P>::T;
-    static constexpr int lo = I == 0 ? 0 : ((T * I / S + 3) & ~3);
-    static constexpr int hi = I + 1 == S ? T : ((T * (I + 1) / S + 3) & ~3);
-};
-
-template <int P, int S, int I> static void m2l_slice_launch(Handle &h, int nc, const float *M, float *L)
-{
-    if constexpr (I < S) {
-        ++h.launches;
-        k_m2l<P, M2LSlice<P, S, I>::lo, M2LSlice<P, S, I>::hi><<<ceil_div((int64_t)nc * 32, 128), 128, 0, h.stream>>>(
-            nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(), M, L);
-        m2l_slice_launch<P, S, I + 1>(h, nc, M, L);
-    }
-}
-
-// At high order the outputs are split over S launches, each recomputing the
-// kernel derivatives and running 1/S of the unrolled contraction: the extra
-// derivative work costs less than the instruction-cache misses of the whole
-// contraction in one kernel.
 template <int P> static int m2l_impl(Handle &h, const float *M, float *L)
 {
+    using HL = HarmLayout<P>;
     const int nc = (int)h.ncells;
-    constexpr int S = P >= 8 ? FMM_M2L_KERNELS : 1;
-    m2l_slice_launch<P, S, 0>(h, nc, M, L);
+    static bool configured[64] = {};
+    if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
+        FMM_CUDA(cudaFuncSetAttribute(k_m2l<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HL::ring_bytes));
+        configured[h.device] = true;
+    }
+    FMM_TRY(h.Mf.reserve((size_t)nc * HL::FP * sizeof(float)));
+    ++h.launches;
+    k_m2l_fold<P><<<ceil_div(nc, 128), 128, 0, h.stream>>>(nc, M, h.c_geom.as<float4>(), h.c_level.as<int>(),
+                                                          h.Mf.as<float>());
+    ++h.launches;
+    k_m2l<P><<<ceil_div((int64_t)nc * 32, 32 * HL::kWarps), 32 * HL::kWarps, HL::ring_bytes, h.stream>>>(
+        nc, h.m2l_off.as<int>(), h.m2l_src.as<int>(), h.c_level.as<int>(), h.c_geom.as<float4>(),
+        h.Mf.as<float4>(), L);
     FMM_CHECK_LAUNCH("m2l");
     return FMM_OK;
 }

@@ -159,6 +159,7 @@ struct Handle {
 
     // expansions and outputs
     DevBuf M, L;          // float[ncells * TP]
+    DevBuf Mf;            // folded multipoles of the harmonic M2L with centre and level, float4[ncells * (ceil(P^2 / 4) + 1)]
 
     // adjoint (fmm_backward): sorted upstream gradients, expansions of the
     // adjoint sources, work items of <= 8 targets

@@ -122,7 +122,7 @@ static void release_merged(Handle &h)
                       &h.c_geom, &h.c_scale, &h.m2l_off, &h.m2l_src, &h.leaf_list, &h.p2p_poff, &h.p2p_ent,
                       &h.p2p_cnt, &h.p2p_items, &h.M, &h.L, &h.phi_sorted, &h.c_tmp, &h.scan_tmp,
                       &h.p2p_off, &h.p2p_src, &h.mu_off, &h.mu_src, &h.os_off, &h.os_src, &h.mu_cnt_tmp,
-                      &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent, &h.os_cnt, &h.racc};
+                      &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent, &h.os_cnt, &h.racc, &h.Mf};
     for (DevBuf *b : bufs) b->release();
 }
 

@@ -16,14 +16,6 @@ namespace fmm {
 
 __device__ __forceinline__ int frame_of(const int *parent, int c) { return parent[c] >= 0 ? parent[c] : c; }
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
 // Bulk-copy (TMA) staging: one lane issues one cp.async.bulk per contiguous
 // run segment (16-byte aligned, a multiple of 16 bytes: float4 particles), the
 // bytes counted on a per-buffer mbarrier that the consumers wait on.
