@@ -73,6 +73,7 @@ struct TravCounters {
     unsigned long long pass_claim[8];   // work-stack pass p: next seed to claim
     unsigned long long p2p_pairs; // sum over P2P pairs of n_target * n_source
     unsigned int overflow;        // bit 0: m2l, bit 1: p2p, bit 2: frontier/spill
+    unsigned int seg_long;        // list grouping: bit 0 / 1 when the m2l / p2p list repeats a (target, source) pair
     unsigned int nleaves;         // leaves found by the leaf-list kernel
     unsigned long long round_count[16];   // frontier size before each seeding round
 };
@@ -136,7 +137,8 @@ struct Handle {
     int64_t m2l_cap = 0, p2p_cap = 0;
     int64_t n_m2l = 0, n_p2p = 0, p2p_pairs = 0;
     // grouped lists
-    DevBuf lkeys, lkeys_alt;   // u64 packed (target << 32 | source) for grouping
+    DevBuf lkeys, lkeys_alt;   // packed (target, source) keys of the radix grouping (long lists only)
+    DevBuf lcnt;               // unsigned[ncells + 1]: per-target counts, then offsets, of the grouping
     DevBuf m2l_src, m2l_off;   // int32 sources, CSR offsets (ncells + 1)
     DevBuf p2p_src, p2p_off;
     DevBuf leaf_list;          // int32 leaf cell ids

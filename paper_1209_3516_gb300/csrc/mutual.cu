@@ -6,7 +6,8 @@
 // (B, A) is), so with FMM_FLAG_MUTUAL each target leaf's list is split into
 //   - its mutual part: sources B > A whose mirror entry (B, A) exists, and
 //   - its one-sided part: B == A, and any entry without a mirror (checked by
-//     a binary search in B's sorted list; none are expected).
+//     a binary search for A in B's sorted list from the entry with B > A; none
+//     are expected).
 // The mutual pass takes, for every work item of A's targets and every source
 // particle s of its mutual runs, both directions of each pair term:
 //   phi_t += q_s / r,  grad_t += q_s (u_s - u_t) / r^3   (target side, registers)
@@ -34,31 +35,43 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 // list split
 // ---------------------------------------------------------------------------
-// Is a in the sorted list src[b0, b1)?
-__device__ __forceinline__ bool list_has(const int *src, int b0, int b1, int a)
+// Position of a in the sorted list src[b0, b1), or -1.
+__device__ __forceinline__ int list_find(const int *src, int b0, int b1, int a)
 {
     while (b0 < b1) {
         const int m = (b0 + b1) >> 1;
         const int v = src[m];
-        if (v == a) return true;
+        if (v == a) return m;
         if (v < a) b0 = m + 1;
         else b1 = m;
     }
-    return false;
+    return -1;
 }
 
-// 0: skip (the mirror's mutual entry covers it), 1: mutual, 2: one-sided
-__device__ __forceinline__ int mutual_kind(const int *off, const int *src, int a, int b)
+// Entry kinds (one byte per list entry, preset to 2): 0 skip (the mirror's
+// mutual entry covers it), 1 mutual, 2 one-sided.  One warp per leaf A; each
+// entry B > A looks A up in B's list: found, the entry is mutual and its
+// mirror is skipped; not found, both stay one-sided.  Entries B == A, and
+// B < A whose mirror was not found, stay one-sided.
+__global__ void k_mutual_mark(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned char *kind)
 {
-    if (b == a) return 2;
-    const bool mirror = list_has(src, off[b], off[b + 1], a);
-    if (!mirror) return 2;
-    return b > a ? 1 : 0;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaves) return;
+    const int t = leaf_list[w];
+    const int eb = off[t], ee = off[t + 1];
+    for (int e = eb + (int)lane_id(); e < ee; e += 32) {
+        const int b = src[e];
+        if (b <= t) continue;
+        const int m = list_find(src, off[b], off[b + 1], t);
+        if (m >= 0) {
+            kind[e] = 1;
+            kind[m] = 0;
+        }
+    }
 }
 
-// One warp per leaf: the kind of each of its entries (kept for the write pass)
-// and its counts of mutual and one-sided entries.
-__global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned char *kind,
+// One warp per leaf: its counts of mutual and one-sided entries.
+__global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off, const unsigned char *kind,
                                unsigned *cnt_mu, unsigned *cnt_os)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -68,8 +81,7 @@ __global__ void k_mutual_count(int nleaves, const int *leaf_list, const int *off
     unsigned nm = 0, no = 0;
     for (int e0 = eb; e0 < ee; e0 += 32) {
         const int e = e0 + (int)lane_id();
-        const int k = e < ee ? mutual_kind(off, src, t, src[e]) : 0;
-        if (e < ee) kind[e] = (unsigned char)k;
+        const int k = e < ee ? kind[e] : 0;
         nm += __popc(__ballot_sync(kFull, k == 1));
         no += __popc(__ballot_sync(kFull, k == 2));
     }
@@ -113,10 +125,13 @@ int build_mutual(Handle &h)
     unsigned *cm = h.mu_cnt_tmp.as<unsigned>(), *co = cm + nc;
     unsigned char *kind = reinterpret_cast<unsigned char *>(co + nc);   // one byte per list entry
     FMM_CUDA(cudaMemsetAsync(cm, 0, (size_t)(2 * nc) * sizeof(unsigned), h.stream));
+    FMM_CUDA(cudaMemsetAsync(kind, 2, (size_t)std::max<int64_t>(h.n_p2p, 1), h.stream));
     const int blocks = ceil_div((int64_t)nl * 32, 256);
     ++h.launches;
-    k_mutual_count<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
-                                                 kind, cm, co);
+    k_mutual_mark<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), h.p2p_src.as<int>(),
+                                                kind);
+    ++h.launches;
+    k_mutual_count<<<blocks, 256, 0, h.stream>>>(nl, h.leaf_list.as<int>(), h.p2p_off.as<int>(), kind, cm, co);
     unsigned *mo = h.mu_off.as<unsigned>(), *oo = h.os_off.as<unsigned>();
     FMM_TRY(scan_exclusive_u32(h, cm, mo, nc, mo + nc));
     FMM_TRY(scan_exclusive_u32(h, co, oo, nc, oo + nc));

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "device_util.cuh"
@@ -271,16 +272,16 @@ __global__ void k_p2p_pairs(const int2 *pairs, int64_t n, const int *pcnt, unsig
     if (lane_id() == 0 && s) atomicAdd(total, s);
 }
 
-// Sort the (target, source) pairs by target, then source, packed as
-// target << cbits | source (32-bit keys whenever 2 cbits <= 32), and split
-// them into CSR form: off[c] .. off[c+1] are the sources of target c.
-template <class K> static int group_list_k(Handle &h, const int2 *pairs, int64_t n, int cbits, DevBuf &src, DevBuf &off)
+// Radix form of the grouping (used only for a list with a repeated
+// (target, source) pair, which the traversal does not emit): sort the (target, source) pairs by target, then
+// source, packed as target << cbits | source (32-bit keys whenever
+// 2 cbits <= 32), and split them into CSR form.
+template <class K> static int group_list_radix_k(Handle &h, const int2 *pairs, int64_t n, int cbits, DevBuf &src,
+                                                 DevBuf &off)
 {
     const int nc = (int)h.ncells;
     FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(K)));
     FMM_TRY(h.lkeys_alt.reserve(std::max<int64_t>(n, 1) * sizeof(K)));
-    FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
-    FMM_TRY(off.reserve((size_t)(nc + 1) * sizeof(int)));
     if (n > 0) {
         ++h.launches;
         k_pack_pairs<K><<<ceil_div(n, 256), 256, 0, h.stream>>>(pairs, n, cbits, h.lkeys.as<K>());
@@ -293,16 +294,167 @@ template <class K> static int group_list_k(Handle &h, const int2 *pairs, int64_t
     }
     ++h.launches;
     k_csr_offsets<K><<<ceil_div(nc + 1, 256), 256, 0, h.stream>>>(h.lkeys.as<K>(), n, cbits, nc, off.as<int>());
-    FMM_CHECK_LAUNCH("group list");
+    FMM_CHECK_LAUNCH("group list (radix)");
     return FMM_OK;
 }
 
-static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
+static int group_list_radix(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
 {
     int cbits = 1;
     while ((1ll << cbits) <= h.ncells) ++cbits;
-    if (2 * cbits <= 32) return group_list_k<uint32_t>(h, pairs, n, cbits, src, off);
-    return group_list_k<uint64_t>(h, pairs, n, cbits, src, off);
+    if (2 * cbits <= 32) return group_list_radix_k<uint32_t>(h, pairs, n, cbits, src, off);
+    return group_list_radix_k<uint64_t>(h, pairs, n, cbits, src, off);
+}
+
+// Counting form of the grouping: per-target counts (warp-aggregated atomics
+// over lanes with equal targets), their exclusive scan as the CSR offsets, an
+// unordered scatter of the sources into a scratch array, then each target's
+// sources written in ascending order by one warp: up to 32 by a bitonic
+// network in registers, beyond that through a bitmap over the sources' index
+// range in shared memory (the sources of one target are distinct cells), in
+// windows of kSegBits indices.  The result equals the radix form's exactly; a
+// repeated source (the traversal emits none) is detected and sends the list
+// to the radix form, which keeps it.
+constexpr int kSegWarps = 8;
+constexpr int kSegWords = 1024;                  // bitmap words per warp
+constexpr int kSegBits = 32 * kSegWords;         // source indices per window
+constexpr int kSegPhys = kSegWords + kSegWords / 32;   // skewed: word j at j + j / 32
+
+__global__ void k_list_count(const int2 *pairs, int64_t n, unsigned *cnt)
+{
+    const int lane = (int)lane_id();
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        const int t = i < n ? pairs[i].x : -1;
+        const unsigned peers = __match_any_sync(kFull, t);
+        if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[t], (unsigned)__popc(peers));
+    }
+}
+
+// tmp[off[t] + slot] = s for every pair (t, s); the slots of a target are
+// handed out downwards from its count (cnt[] ends at zero).
+__global__ void k_list_scatter(const int2 *pairs, int64_t n, const unsigned *off, unsigned *cnt, int *tmp)
+{
+    const int lane = (int)lane_id();
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        int2 p = make_int2(-1, 0);
+        if (i < n) p = pairs[i];
+        const unsigned peers = __match_any_sync(kFull, p.x);
+        const int leader = __ffs(peers) - 1;
+        const unsigned k = (unsigned)__popc(peers);
+        unsigned top = 0;
+        if (p.x >= 0 && lane == leader) top = atomicSub(&cnt[p.x], k);
+        top = __shfl_sync(kFull, top, leader);
+        if (p.x >= 0) tmp[off[p.x] + top - k + __popc(peers & lanemask_lt())] = p.y;
+    }
+}
+
+__device__ __forceinline__ int warp_sort32(int v, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int o = __shfl_xor_sync(kFull, v, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            v = (lower == up) ? min(v, o) : max(v, o);
+        }
+    return v;
+}
+
+__global__ void __launch_bounds__(kSegWarps * 32) k_list_segsort(int nc, const unsigned *off, const int *tmp,
+                                                                  int *src, unsigned *repeated, unsigned bit)
+{
+    __shared__ unsigned bitmap[kSegWarps][kSegPhys];
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= nc) return;
+    const int lane = (int)lane_id();
+    const unsigned b = off[t], L = off[t + 1] - b;
+    if (L == 0) return;
+    const int *si = tmp + b;
+    int *so = src + b;
+    if (L <= 32) {
+        int v = lane < (int)L ? si[lane] : INT_MAX;
+        v = warp_sort32(v, lane);
+        if (lane < (int)L) so[lane] = v;
+        return;
+    }
+    int lo = INT_MAX, hi = 0;
+    for (unsigned i = lane; i < L; i += 32) {
+        const int v = si[i];
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    lo = __reduce_min_sync(kFull, lo);
+    hi = __reduce_max_sync(kFull, hi);
+    unsigned *bm = bitmap[threadIdx.x >> 5];
+    unsigned written = 0;
+    for (int c0 = lo; c0 <= hi; c0 += kSegBits) {
+        const int nw = min(kSegWords, (hi - c0) / 32 + 1);   // words of this window
+        for (int j = lane; j < nw; j += 32) bm[j + (j >> 5)] = 0u;
+        __syncwarp();
+        for (unsigned i = lane; i < L; i += 32) {
+            const int v = si[i] - c0;
+            if (v >= 0 && v < 32 * nw) atomicOr(&bm[(v >> 5) + (v >> 10)], 1u << (v & 31));
+        }
+        __syncwarp();
+        // lane l owns the words [l per, (l + 1) per): counts, their scan, then the indices in order
+        const int per = (nw + 31) / 32;
+        const int j0 = min(lane * per, nw), j1 = min(j0 + per, nw);
+        unsigned c = 0;
+        for (int j = j0; j < j1; ++j) c += __popc(bm[j + (j >> 5)]);
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += u;
+        }
+        unsigned pos = written + incl - c;
+        for (int j = j0; j < j1; ++j) {
+            unsigned x = bm[j + (j >> 5)];
+            while (x) {
+                so[pos++] = c0 + 32 * j + (__ffs(x) - 1);
+                x &= x - 1u;
+            }
+        }
+        written += __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+    }
+    if (written != L && lane == 0) atomicOr(repeated, bit);
+}
+
+// Group the (target, source) pairs by target into CSR form: off[c] .. off[c+1]
+// are the sources of target c, ascending.  A repeated (target, source) pair
+// sets `bit` in ctr->seg_long (read at the end of the list phase, which then
+// regroups that list with the radix form).
+static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off, unsigned bit)
+{
+    const int nc = (int)h.ncells;
+    FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
+    FMM_TRY(off.reserve((size_t)(nc + 1) * sizeof(int)));
+    FMM_TRY(h.lcnt.reserve((size_t)(nc + 1) * sizeof(unsigned)));
+    FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
+    unsigned *cnt = h.lcnt.as<unsigned>();
+    unsigned *offu = reinterpret_cast<unsigned *>(off.as<int>());
+    FMM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nc + 1) * sizeof(unsigned), h.stream));
+    const int gb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(n, 256), 1), (int64_t)h.num_sms * 16);
+    if (n > 0) {
+        ++h.launches;
+        k_list_count<<<gb, 256, 0, h.stream>>>(pairs, n, cnt);
+    }
+    FMM_TRY(scan_exclusive_u32(h, cnt, offu, nc + 1, nullptr));
+    if (n > 0) {
+        ++h.launches;
+        k_list_scatter<<<gb, 256, 0, h.stream>>>(pairs, n, offu, cnt, h.lkeys.as<int>());
+        ++h.launches;
+        k_list_segsort<<<ceil_div((int64_t)nc * 32, kSegWarps * 32), kSegWarps * 32, 0, h.stream>>>(
+            nc, offu, h.lkeys.as<int>(), src.as<int>(), &h.counters.as<TravCounters>()->seg_long, bit);
+    }
+    FMM_CHECK_LAUNCH("group list");
+    return FMM_OK;
 }
 
 int build_lists(Handle &h)
@@ -445,8 +597,8 @@ int build_lists(Handle &h)
     phase_end(h, FMM_PHASE_TRAVERSE);
 
     phase_begin(h, FMM_PHASE_LISTS);
-    FMM_TRY(group_list(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off));
-    FMM_TRY(group_list(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off));
+    FMM_TRY(group_list(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off, 1u));
+    FMM_TRY(group_list(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off, 2u));
     // P2P particle pairs (for the counters)
     FMM_CUDA(cudaMemsetAsync(&ctr->p2p_pairs, 0, sizeof(unsigned long long), h.stream));
     if (h.n_p2p > 0) {
@@ -459,6 +611,11 @@ int build_lists(Handle &h)
     FMM_CUDA(cudaStreamSynchronize(h.stream));
     h.p2p_pairs = (int64_t)hc->p2p_pairs;
     h.nleaves = hc->nleaves;
+    if (hc->seg_long) {
+        // a repeated (target, source) pair: regroup that list by radix sort
+        if (hc->seg_long & 1u) FMM_TRY(group_list_radix(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off));
+        if (hc->seg_long & 2u) FMM_TRY(group_list_radix(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off));
+    }
     phase_end(h, FMM_PHASE_LISTS);
     return FMM_OK;
 }
