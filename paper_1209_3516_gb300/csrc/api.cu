@@ -227,7 +227,7 @@ int fmm_destroy(fmm_handle *w)
     if (h.stream) cudaStreamSynchronize(h.stream);
     else cudaDeviceSynchronize();
     DevBuf *bufs[] = {&h.norm, &h.bbox_part, &h.err_flag, &h.keys, &h.keys_alt, &h.idx, &h.idx_alt, &h.sort_hist,
-                      &h.scan_tmp, &h.pos_unsorted, &h.pos, &h.perm, &h.c_prefix, &h.c_level, &h.c_pbeg, &h.c_pcnt,
+                      &h.scan_tmp, &h.pos_unsorted, &h.u_unsorted, &h.u_sorted, &h.pos, &h.perm, &h.c_prefix, &h.c_level, &h.c_pbeg, &h.c_pcnt,
                       &h.c_cbeg, &h.c_ccnt, &h.c_parent, &h.c_geom, &h.c_kids, &h.c_r2bits, &h.c_tmp, &h.leaf_of,
                       &h.counters, &h.front[0], &h.front[1], &h.m2l_raw, &h.p2p_raw, &h.lkeys, &h.lkeys_alt, &h.lcnt,
                       &h.m2l_src, &h.m2l_off, &h.p2p_src, &h.p2p_off, &h.leaf_list, &h.p2p_items, &h.p2p_poff, &h.p2p_ent, &h.p2p_cnt,

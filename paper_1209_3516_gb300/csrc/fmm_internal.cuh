@@ -74,6 +74,7 @@ struct TravCounters {
     unsigned long long p2p_pairs; // sum over P2P pairs of n_target * n_source
     unsigned int overflow;        // bit 0: m2l, bit 1: p2p, bit 2: frontier/spill
     unsigned int seg_long;        // list grouping: bit 0 / 1 when the m2l / p2p list repeats a (target, source) pair
+    unsigned int reg_max[2];      // traversal: largest region count of the m2l / p2p list
     unsigned int nleaves;         // leaves found by the leaf-list kernel
     unsigned long long round_count[16];   // frontier size before each seeding round
 };
@@ -113,6 +114,7 @@ struct Handle {
     DevBuf sort_hist;             // u32[256 * tiles]
     DevBuf scan_tmp;              // u32 scratch of the device-wide scan
     DevBuf pos_unsorted;          // float4[N]
+    DevBuf u_unsorted, u_sorted;  // double[3][N]: normalised FP64 coordinates, input / Morton order
     DevBuf pos;                   // float4[N] sorted (u, q)
     DevBuf perm;                  // int32[N]
 
@@ -134,7 +136,9 @@ struct Handle {
     DevBuf front[2];      // int2 frontier / seed / spill arrays
     int64_t front_cap = 0;
     DevBuf m2l_raw, p2p_raw;   // int2 pairs as emitted
-    int64_t m2l_cap = 0, p2p_cap = 0;
+    int64_t m2l_cap = 0, p2p_cap = 0;   // per-region capacities of the traversal's list buffers
+    DevBuf trav_reg;                    // unsigned[2 * regions]: region counts of the traversal
+    DevBuf ldense;                      // int2[n]: a list compacted from its regions (radix regrouping only)
     int64_t n_m2l = 0, n_p2p = 0, p2p_pairs = 0;
     // grouped lists
     DevBuf lkeys, lkeys_alt;   // packed (target, source) keys of the radix grouping (long lists only)

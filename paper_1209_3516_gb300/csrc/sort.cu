@@ -116,10 +116,63 @@ __global__ void k_scan_apply(const unsigned *in, int64_t n, const unsigned *bloc
     }
 }
 
+// One block for arrays of at most one tile (one launch instead of three);
+// longer arrays take the three-kernel scan, which is faster from two tiles on.
+constexpr int64_t kScanSingleMax = kScanChunk;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const unsigned *in, int64_t n, unsigned *out,
+                                                              unsigned *total)
+{
+    __shared__ unsigned tile[kScanChunk];
+    unsigned carry = 0;
+    unsigned nxt[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = k * kScanThreads + threadIdx.x;
+        nxt[k] = i < n ? in[i] : 0u;
+    }
+    for (int64_t base = 0; base < n; base += kScanChunk) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) tile[k * kScanThreads + threadIdx.x] = nxt[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t i = base + kScanChunk + k * kScanThreads + threadIdx.x;
+            nxt[k] = i < n ? in[i] : 0u;
+        }
+        unsigned loc[kScanItems];
+        unsigned s = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            loc[k] = s;
+            s += tile[threadIdx.x * kScanItems + k];
+        }
+        unsigned tot;
+        const unsigned ex = block_exclusive_scan(s, &tot) + carry;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) tile[threadIdx.x * kScanItems + k] = ex + loc[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t i = base + k * kScanThreads + threadIdx.x;
+            if (i < n) out[i] = tile[k * kScanThreads + threadIdx.x];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, unsigned *total_dev)
 {
     if (n <= 0) {
         if (total_dev) FMM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(unsigned), h.stream));
+        return FMM_OK;
+    }
+    if (n <= kScanSingleMax) {
+        ++h.launches;
+        k_scan_single<<<1, kScanThreads, 0, h.stream>>>(in, n, out, total_dev);
+        FMM_CHECK_LAUNCH("scan");
         return FMM_OK;
     }
     const int nb = ceil_div(n, kScanChunk);

@@ -32,9 +32,9 @@
 namespace fmm {
 
 constexpr unsigned kOvM2L = 1u, kOvP2P = 2u, kOvNext = 4u;
-constexpr int kStackCap = 256;      // pairs per warp stack
+constexpr int kStackCap = 128;      // pairs per warp stack (24 bytes each)
 constexpr int kStackWarps = 8;      // warps per block of the work-stack kernel
-constexpr int kStackBlocksPerSM = 8;   // 64 resident warps per SM (16 KiB shared memory per block)
+constexpr int kStackBlocksPerSM = 8;   // 64 resident warps per SM (24 KiB shared memory, <= 32 registers)
 #ifndef FMM_SEED_BUDGET
 #define FMM_SEED_BUDGET 128
 #endif
@@ -88,6 +88,12 @@ __device__ __forceinline__ bool split_target(const Cell &A, const Cell &B)
     return B.k.y == 0 || (A.k.y != 0 && A.g.w > B.g.w);
 }
 
+// The emitted M2L and P2P pairs go to per-block regions of the list buffers:
+// region r of a list holds cap entries from r cap on, counted in reg[r] (M2L)
+// and reg[nreg + r] (P2P), one region per block of the work-stack kernel,
+// which appends to it through a shared-memory counter; block b of a seeding
+// round appends to region b mod nreg through global atomics.  (One global
+// counter for all appends made the traversal wait on the serialised atomics.)
 struct TravArgs {
     const float4 *geom;
     const int2 *kids;
@@ -95,15 +101,35 @@ struct TravArgs {
     float theta;
     long long hybrid_min;   // < 0: Algorithm 4 as printed
     int2 *m2l;
-    unsigned long long m2l_cap;
     int2 *p2p;
-    unsigned long long p2p_cap;
+    unsigned cap_m2l, cap_p2p;   // region capacities (multiples of 32)
+    unsigned *reg;               // region counts, 2 nreg
+    int nreg;
     int2 *next;
     unsigned long long next_cap;
     unsigned long long *n_next;   // count of pairs written to next (seeding round or work-stack pass)
     unsigned long long *claim;    // work-stack pass: next seed to claim
     TravCounters *ctr;
 };
+
+// Warp-aggregated append to a region with a 32-bit counter (global or shared
+// memory); entries past the capacity are dropped and flagged, the counter
+// still counts them.  Every lane of the warp calls it.
+__device__ __forceinline__ void region_append(bool pred, int2 val, int2 *region, unsigned cap, unsigned *count,
+                                              unsigned *overflow, unsigned bit)
+{
+    const unsigned m = __ballot_sync(kFull, pred);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (pred) {
+        const unsigned i = base + __popc(m & lanemask_lt());
+        if (i < cap) region[i] = val;
+        else atomicOr(overflow, bit);
+    }
+}
 
 // Child pair j (0..7) of a popped pair; returns false when the split cell has fewer children.
 __device__ __forceinline__ bool child_pair(const TravArgs &a, int2 pr, int j, int2 &np, Cell &ca, Cell &cb)
@@ -143,20 +169,42 @@ __global__ void k_dtt_round(const int2 *front, const unsigned long long *nfront_
             Cell ca, cb;
             if (child_pair(a, front[t >> 3], (int)(t & 7ull), np, ca, cb)) kind = interact(ca, cb, a.theta, a.hybrid_min);
         }
-        warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
-        warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
+        const int rg = (int)(blockIdx.x % (unsigned)a.nreg);
+        region_append(kind == 1, np, a.p2p + (size_t)rg * a.cap_p2p, a.cap_p2p, &a.reg[a.nreg + rg],
+                      &a.ctr->overflow, kOvP2P);
+        region_append(kind == 2, np, a.m2l + (size_t)rg * a.cap_m2l, a.cap_m2l, &a.reg[rg], &a.ctr->overflow,
+                      kOvM2L);
         warp_append(kind == 3, np, a.next, a.next_cap, nnext_p, &a.ctr->overflow, kOvNext);
     }
 }
 
+// A stack entry of the work-stack kernel: the pair, both cells' children
+// (first child << 4 | child count) and both radii, so that the split rule
+// needs no load and one round of loads serves a step: the j-th child of the
+// cell that is split and the other cell's centre (and particle count).
+__device__ __forceinline__ int pack_kids(int2 k) { return (int)(((unsigned)k.x << 4) | (unsigned)k.y); }
+__device__ __forceinline__ int2 unpack_kids(int v) { return make_int2((int)((unsigned)v >> 4), v & 15); }
+
 // Persistent work-stack kernel; the seed count is read from device memory.
-__global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seeds, const unsigned long long *nseeds_p,
-                                                                TravArgs a)
+__global__ void __launch_bounds__(kStackWarps * 32, kStackBlocksPerSM) k_dtt_stack(const int2 *seeds,
+                                                                                   const unsigned long long *nseeds_p,
+                                                                                   TravArgs a)
 {
     const unsigned long long nseeds = min(*nseeds_p, a.next_cap);
-    __shared__ int2 stack[kStackWarps][kStackCap];
+    __shared__ int4 stack[kStackWarps][kStackCap];     // a, b, packed children of a and b
+    __shared__ float2 radii[kStackWarps][kStackCap];   // radius of a, of b
+    __shared__ unsigned s_count[2];                    // this block's region counts (M2L, P2P)
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    int2 *st = stack[w];
+    if (threadIdx.x == 0) {
+        s_count[0] = a.reg[blockIdx.x];
+        s_count[1] = a.reg[a.nreg + blockIdx.x];
+    }
+    __syncthreads();
+    int2 *const reg_m2l = a.m2l + (size_t)blockIdx.x * a.cap_m2l;
+    int2 *const reg_p2p = a.p2p + (size_t)blockIdx.x * a.cap_p2p;
+    const bool with_n = a.hybrid_min >= 0;   // particle counts matter only to the hybrid rule
+    int4 *st = stack[w];
+    float2 *sr = radii[w];
     int top = 0, steps = 0;
     for (;;) {
         if (top > 0 && steps >= kSeedBudget) {
@@ -165,7 +213,7 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
             if (lane == 0) base = atomicAdd(a.n_next, (unsigned long long)top);
             base = __shfl_sync(kFull, base, 0);
             for (int i = (int)lane; i < top; i += 32) {
-                if (base + i < a.next_cap) a.next[base + i] = st[i];
+                if (base + i < a.next_cap) a.next[base + i] = make_int2(st[i].x, st[i].y);
                 else atomicOr(&a.ctr->overflow, kOvNext);
             }
             top = 0;
@@ -176,7 +224,11 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
             if (lane == 0) s = atomicAdd(a.claim, 1ull);
             s = __shfl_sync(kFull, s, 0);
             if (s >= nseeds) break;
-            if (lane == 0) st[0] = seeds[s];
+            if (lane == 0) {
+                const int2 sd = seeds[s];
+                st[0] = make_int4(sd.x, sd.y, pack_kids(a.kids[sd.x]), pack_kids(a.kids[sd.y]));
+                sr[0] = make_float2(a.geom[sd.x].w, a.geom[sd.y].w);
+            }
             top = 1;
             steps = 0;
             __syncwarp();
@@ -187,24 +239,103 @@ __global__ void __launch_bounds__(kStackWarps * 32) k_dtt_stack(const int2 *seed
         const int p = (int)(lane >> 3), j = (int)(lane & 7u);
         int kind = 0;
         int2 np = make_int2(0, 0);
-        int2 pr = make_int2(0, 0);
-        if (p < npop) pr = st[top + p];
+        Cell ca, cb;
+        int4 pr = make_int4(0, 0, 0, 0);
+        float2 rr = make_float2(0.f, 0.f);
+        if (p < npop) {
+            pr = st[top + p];
+            rr = sr[top + p];
+        }
         __syncwarp();   // every popped entry is read before pushes overwrite the slots
         if (p < npop) {
-            Cell ca, cb;
-            if (child_pair(a, pr, j, np, ca, cb)) kind = interact(ca, cb, a.theta, a.hybrid_min);
+            Cell A, B;
+            A.k = unpack_kids(pr.z);
+            B.k = unpack_kids(pr.w);
+            A.g.w = rr.x;
+            B.g.w = rr.y;
+            if (split_target(A, B)) {
+                if (j < A.k.y) {
+                    np = make_int2(A.k.x + j, pr.y);
+                    ca.g = a.geom[np.x];
+                    ca.k = a.kids[np.x];
+                    ca.n = with_n ? a.pcnt[np.x] : 0;
+                    cb.g = a.geom[pr.y];
+                    cb.k = B.k;
+                    cb.n = with_n ? a.pcnt[pr.y] : 0;
+                    kind = interact(ca, cb, a.theta, a.hybrid_min);
+                }
+            } else if (j < B.k.y) {
+                np = make_int2(pr.x, B.k.x + j);
+                ca.g = a.geom[pr.x];
+                ca.k = A.k;
+                ca.n = with_n ? a.pcnt[pr.x] : 0;
+                cb.g = a.geom[np.y];
+                cb.k = a.kids[np.y];
+                cb.n = with_n ? a.pcnt[np.y] : 0;
+                kind = interact(ca, cb, a.theta, a.hybrid_min);
+            }
         }
-        warp_append(kind == 1, np, a.p2p, a.p2p_cap, &a.ctr->n_p2p, &a.ctr->overflow, kOvP2P);
-        warp_append(kind == 2, np, a.m2l, a.m2l_cap, &a.ctr->n_m2l, &a.ctr->overflow, kOvM2L);
+        region_append(kind == 1, np, reg_p2p, a.cap_p2p, &s_count[1], &a.ctr->overflow, kOvP2P);
+        region_append(kind == 2, np, reg_m2l, a.cap_m2l, &s_count[0], &a.ctr->overflow, kOvM2L);
         const unsigned push = __ballot_sync(kFull, kind == 3);
         const int npush = __popc(push);
         if (top + npush <= kStackCap) {
-            if (kind == 3) st[top + __popc(push & lanemask_lt())] = np;
+            if (kind == 3) {
+                const int slot = top + __popc(push & lanemask_lt());
+                st[slot] = make_int4(np.x, np.y, pack_kids(ca.k), pack_kids(cb.k));
+                sr[slot] = make_float2(ca.g.w, cb.g.w);
+            }
             top += npush;
         } else {
             warp_append(kind == 3, np, a.next, a.next_cap, a.n_next, &a.ctr->overflow, kOvNext);
         }
         __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.reg[blockIdx.x] = s_count[0];
+        a.reg[a.nreg + blockIdx.x] = s_count[1];
+    }
+}
+
+// Totals and largest region of both lists (one block of 256 threads).
+__global__ void k_region_totals(int nreg, const unsigned *reg, TravCounters *ctr)
+{
+    __shared__ unsigned long long s_sum[2][8];
+    __shared__ unsigned s_max[2][8];
+    unsigned long long s0 = 0, s1 = 0;
+    unsigned m0 = 0, m1 = 0;
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
+        s0 += reg[r];
+        s1 += reg[nreg + r];
+        m0 = max(m0, reg[r]);
+        m1 = max(m1, reg[nreg + r]);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    m0 = __reduce_max_sync(kFull, m0);
+    m1 = __reduce_max_sync(kFull, m1);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) {
+        s_sum[0][w] = s0;
+        s_sum[1][w] = s1;
+        s_max[0][w] = m0;
+        s_max[1][w] = m1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t0 = 0, t1 = 0;
+        unsigned x0 = 0, x1 = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t0 += s_sum[0][k];
+            t1 += s_sum[1][k];
+            x0 = max(x0, s_max[0][k]);
+            x1 = max(x1, s_max[1][k]);
+        }
+        ctr->n_m2l = t0;
+        ctr->n_p2p = t1;
+        ctr->reg_max[0] = x0;
+        ctr->reg_max[1] = x1;
     }
 }
 
@@ -261,15 +392,48 @@ __global__ void k_leaf_list(int nc, const int *ccnt, int *leaf_list, unsigned *n
     if (leaf) leaf_list[base + __popc(m & lanemask_lt())] = c;
 }
 
-__global__ void k_p2p_pairs(const int2 *pairs, int64_t n, const int *pcnt, unsigned long long *total)
+// A list as the traversal leaves it: region r holds cnt[r] pairs from r cap on.
+struct RegionList {
+    const int2 *pairs;
+    const unsigned *cnt;
+    unsigned cap;   // multiple of 32
+    int nreg;
+};
+
+// Walk over a region list: block b takes regions b, b + gridDim.x, ..., its
+// warps the 32-entry chunks of each; f(lane's pair, valid, region, index) is
+// called by every lane of a chunk.
+template <class F> __device__ __forceinline__ void for_each_chunk(const RegionList &L, F f)
+{
+    const unsigned lane = lane_id();
+    for (int r = blockIdx.x; r < L.nreg; r += gridDim.x) {
+        const unsigned n = min(L.cnt[r], L.cap);
+        const int2 *pr = L.pairs + (size_t)r * L.cap;
+        for (unsigned off = threadIdx.x - lane; off < n; off += blockDim.x) {
+            const unsigned k = off + lane;
+            const bool valid = k < n;
+            const int2 p = valid ? pr[k] : make_int2(-1, 0);
+            f(p, valid, r, k);
+        }
+    }
+}
+
+__global__ void k_p2p_pairs(RegionList L, const int *pcnt, unsigned long long *total)
 {
     unsigned long long s = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int2 p = pairs[i];
-        s += (unsigned long long)pcnt[p.x] * (unsigned long long)pcnt[p.y];
-    }
+    for_each_chunk(L, [&](int2 p, bool valid, int, unsigned) {
+        if (valid) s += (unsigned long long)pcnt[p.x] * (unsigned long long)pcnt[p.y];
+    });
     s = warp_sum(s);
     if (lane_id() == 0 && s) atomicAdd(total, s);
+}
+
+// dense[roff[r] + k] = pair k of region r
+__global__ void k_compact_regions(RegionList L, const unsigned *roff, int2 *dense)
+{
+    for_each_chunk(L, [&](int2 p, bool valid, int r, unsigned k) {
+        if (valid) dense[roff[r] + k] = p;
+    });
 }
 
 // Radix form of the grouping (used only for a list with a repeated
@@ -298,8 +462,16 @@ template <class K> static int group_list_radix_k(Handle &h, const int2 *pairs, i
     return FMM_OK;
 }
 
-static int group_list_radix(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off)
+static int group_list_radix(Handle &h, const RegionList &L, int64_t n, DevBuf &src, DevBuf &off)
 {
+    // the regions back to back first
+    FMM_TRY(h.ldense.reserve(std::max<int64_t>(n, 1) * sizeof(int2) + (size_t)(L.nreg + 1) * sizeof(unsigned)));
+    int2 *dense = h.ldense.as<int2>();
+    unsigned *roff = reinterpret_cast<unsigned *>(dense + std::max<int64_t>(n, 1));
+    FMM_TRY(scan_exclusive_u32(h, L.cnt, roff, L.nreg, nullptr));
+    ++h.launches;
+    k_compact_regions<<<L.nreg, 256, 0, h.stream>>>(L, roff, dense);
+    const int2 *pairs = dense;
     int cbits = 1;
     while ((1ll << cbits) <= h.ncells) ++cbits;
     if (2 * cbits <= 32) return group_list_radix_k<uint32_t>(h, pairs, n, cbits, src, off);
@@ -320,28 +492,21 @@ constexpr int kSegWords = 1024;                  // bitmap words per warp
 constexpr int kSegBits = 32 * kSegWords;         // source indices per window
 constexpr int kSegPhys = kSegWords + kSegWords / 32;   // skewed: word j at j + j / 32
 
-__global__ void k_list_count(const int2 *pairs, int64_t n, unsigned *cnt)
+__global__ void k_list_count(RegionList L, unsigned *cnt)
 {
     const int lane = (int)lane_id();
-    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < n; base += nwarps * 32) {
-        const int64_t i = base + lane;
-        const int t = i < n ? pairs[i].x : -1;
-        const unsigned peers = __match_any_sync(kFull, t);
-        if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[t], (unsigned)__popc(peers));
-    }
+    for_each_chunk(L, [&](int2 p, bool, int, unsigned) {
+        const unsigned peers = __match_any_sync(kFull, p.x);
+        if (p.x >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[p.x], (unsigned)__popc(peers));
+    });
 }
 
 // tmp[off[t] + slot] = s for every pair (t, s); the slots of a target are
 // handed out downwards from its count (cnt[] ends at zero).
-__global__ void k_list_scatter(const int2 *pairs, int64_t n, const unsigned *off, unsigned *cnt, int *tmp)
+__global__ void k_list_scatter(RegionList L, const unsigned *off, unsigned *cnt, int *tmp)
 {
     const int lane = (int)lane_id();
-    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane); base < n; base += nwarps * 32) {
-        const int64_t i = base + lane;
-        int2 p = make_int2(-1, 0);
-        if (i < n) p = pairs[i];
+    for_each_chunk(L, [&](int2 p, bool, int, unsigned) {
         const unsigned peers = __match_any_sync(kFull, p.x);
         const int leader = __ffs(peers) - 1;
         const unsigned k = (unsigned)__popc(peers);
@@ -349,7 +514,7 @@ __global__ void k_list_scatter(const int2 *pairs, int64_t n, const unsigned *off
         if (p.x >= 0 && lane == leader) top = atomicSub(&cnt[p.x], k);
         top = __shfl_sync(kFull, top, leader);
         if (p.x >= 0) tmp[off[p.x] + top - k + __popc(peers & lanemask_lt())] = p.y;
-    }
+    });
 }
 
 __device__ __forceinline__ int warp_sort32(int v, int lane)
@@ -430,7 +595,7 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_list_segsort(int nc, const u
 // are the sources of target c, ascending.  A repeated (target, source) pair
 // sets `bit` in ctr->seg_long (read at the end of the list phase, which then
 // regroups that list with the radix form).
-static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevBuf &off, unsigned bit)
+static int group_list(Handle &h, const RegionList &L, int64_t n, DevBuf &src, DevBuf &off, unsigned bit)
 {
     const int nc = (int)h.ncells;
     FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
@@ -440,15 +605,15 @@ static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevB
     unsigned *cnt = h.lcnt.as<unsigned>();
     unsigned *offu = reinterpret_cast<unsigned *>(off.as<int>());
     FMM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nc + 1) * sizeof(unsigned), h.stream));
-    const int gb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(n, 256), 1), (int64_t)h.num_sms * 16);
+    const int gb = L.nreg;   // one block per region
     if (n > 0) {
         ++h.launches;
-        k_list_count<<<gb, 256, 0, h.stream>>>(pairs, n, cnt);
+        k_list_count<<<gb, 256, 0, h.stream>>>(L, cnt);
     }
     FMM_TRY(scan_exclusive_u32(h, cnt, offu, nc + 1, nullptr));
     if (n > 0) {
         ++h.launches;
-        k_list_scatter<<<gb, 256, 0, h.stream>>>(pairs, n, offu, cnt, h.lkeys.as<int>());
+        k_list_scatter<<<gb, 256, 0, h.stream>>>(L, offu, cnt, h.lkeys.as<int>());
         ++h.launches;
         k_list_segsort<<<ceil_div((int64_t)nc * 32, kSegWarps * 32), kSegWarps * 32, 0, h.stream>>>(
             nc, offu, h.lkeys.as<int>(), src.as<int>(), &h.counters.as<TravCounters>()->seg_long, bit);
@@ -460,6 +625,11 @@ static int group_list(Handle &h, const int2 *pairs, int64_t n, DevBuf &src, DevB
 int build_lists(Handle &h)
 {
     const int nc = (int)h.ncells;
+    if (nc >= (1 << 28)) {
+        // the work stack packs a cell's first child into 28 bits
+        set_error("dual tree traversal: more than 2^28 cells");
+        return FMM_ERR_CAPACITY;
+    }
     FMM_TRY(h.c_kids.reserve(nc * sizeof(int2)));
     ++h.launches;
     k_pack_kids<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_cbeg.as<int>(), h.c_ccnt.as<int>(),
@@ -477,26 +647,31 @@ int build_lists(Handle &h)
     FMM_CHECK_LAUNCH("leaf list");
 
     phase_begin(h, FMM_PHASE_TRAVERSE);
+    const int stack_blocks = h.num_sms * kStackBlocksPerSM;
+    const int nreg = stack_blocks;   // one region per work-stack block
+    auto round32 = [](int64_t v) { return (v + 31) / 32 * 32; };
     if (h.m2l_cap == 0) {
-        h.m2l_cap = (int64_t)nc * 64 + 1024;
-        h.p2p_cap = (int64_t)nc * 32 + 1024;
+        h.m2l_cap = round32(((int64_t)nc * 64 + 1024) / nreg + 256);
+        h.p2p_cap = round32(((int64_t)nc * 32 + 1024) / nreg + 256);
         h.front_cap = (int64_t)nc * 8 + 4096;
     }
-    const int stack_blocks = h.num_sms * kStackBlocksPerSM;
     // seeding rounds: each splits one side of every frontier pair, so the frontier
     // grows by at most 8x per round; enough rounds for ~4 seeds per resident warp
     const int64_t seed_target = (int64_t)stack_blocks * kStackWarps * 4;
     int nrounds = 0;
     for (int64_t f = 1; f < seed_target && nrounds < 2 * h.nlevels && nrounds < 15; f *= 8) ++nrounds;
     const int round_blocks = h.num_sms * 16;
+    FMM_TRY(h.trav_reg.reserve((size_t)2 * nreg * sizeof(unsigned)));
+    unsigned *reg = h.trav_reg.as<unsigned>();
     for (int attempt = 0;; ++attempt) {
-        FMM_TRY(h.m2l_raw.reserve(h.m2l_cap * sizeof(int2)));
-        FMM_TRY(h.p2p_raw.reserve(h.p2p_cap * sizeof(int2)));
+        FMM_TRY(h.m2l_raw.reserve((size_t)nreg * h.m2l_cap * sizeof(int2)));
+        FMM_TRY(h.p2p_raw.reserve((size_t)nreg * h.p2p_cap * sizeof(int2)));
         FMM_TRY(h.front[0].reserve(h.front_cap * sizeof(int2)));
         FMM_TRY(h.front[1].reserve(h.front_cap * sizeof(int2)));
         // zero the counters, keeping the leaf count found above
         FMM_CUDA(cudaMemsetAsync(ctr, 0, offsetof(TravCounters, nleaves), h.stream));
         FMM_CUDA(cudaMemsetAsync(&ctr->round_count[0], 0, sizeof(ctr->round_count), h.stream));
+        FMM_CUDA(cudaMemsetAsync(reg, 0, (size_t)2 * nreg * sizeof(unsigned), h.stream));
         TravArgs a;
         a.geom = h.c_geom.as<float4>();
         a.kids = h.c_kids.as<int2>();
@@ -504,17 +679,22 @@ int build_lists(Handle &h)
         a.theta = h.theta;
         a.hybrid_min = h.hybrid_min_pairs;
         a.m2l = h.m2l_raw.as<int2>();
-        a.m2l_cap = h.m2l_cap;
         a.p2p = h.p2p_raw.as<int2>();
-        a.p2p_cap = h.p2p_cap;
+        a.cap_m2l = (unsigned)h.m2l_cap;
+        a.cap_p2p = (unsigned)h.p2p_cap;
+        a.reg = reg;
+        a.nreg = nreg;
         a.next_cap = h.front_cap;
         a.n_next = nullptr;
         a.claim = nullptr;
         a.ctr = ctr;
         if (h.nlevels <= 1) {
-            // the root is a leaf: the single P2P pair (root, root)
+            // the root is a leaf: the single P2P pair (root, root), region 0
             int2 rp = make_int2(0, 0);
+            h.pinned->level_total = 1u;
             FMM_CUDA(cudaMemcpyAsync(h.p2p_raw.p, &rp, sizeof(int2), cudaMemcpyHostToDevice, h.stream));
+            FMM_CUDA(cudaMemcpyAsync(reg + nreg, &h.pinned->level_total, sizeof(unsigned), cudaMemcpyHostToDevice,
+                                     h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));
             h.n_m2l = 0;
             h.n_p2p = 1;
@@ -561,6 +741,8 @@ int build_lists(Handle &h)
                                                                              &ctr->pass_count[p], a);
                 cur ^= 1;
             }
+            ++h.launches;
+            k_region_totals<<<1, 256, 0, h.stream>>>(nreg, reg, ctr);
             FMM_CHECK_LAUNCH("dtt stack");
             FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
             FMM_CUDA(cudaStreamSynchronize(h.stream));
@@ -579,32 +761,40 @@ int build_lists(Handle &h)
         if (attempt >= 12) {
             char msg[256];
             snprintf(msg, sizeof(msg),
-                     "dual tree traversal: buffers still overflow after %d regrowths (flags %u, caps m2l %lld "
-                     "p2p %lld frontier %lld)",
+                     "dual tree traversal: buffers still overflow after %d regrowths (flags %u, region caps m2l %lld "
+                     "p2p %lld, frontier %lld)",
                      attempt, hc->overflow, (long long)h.m2l_cap, (long long)h.p2p_cap, (long long)h.front_cap);
             set_error(msg);
             return FMM_ERR_CAPACITY;
         }
-        // The traversal stopped at the first overflow, so the counters are lower
-        // bounds: at least double what overflowed and run again.
+        // The region counters keep counting past their capacity, so the largest
+        // is the size needed (a lower bound if the traversal was cut short by a
+        // frontier overflow): grow to 5/4 of it, at least double, and run again.
         unsigned long long max_round = 0;
         for (int r = 0; r <= nrounds; ++r) max_round = std::max(max_round, hc->round_count[r]);
         for (int p = 0; p <= kPassesPerSync; ++p) max_round = std::max(max_round, hc->pass_count[p]);
-        if (hc->overflow & kOvM2L) h.m2l_cap = std::max<int64_t>(h.m2l_cap * 2, (int64_t)(hc->n_m2l * 3 / 2) + 1024);
-        if (hc->overflow & kOvP2P) h.p2p_cap = std::max<int64_t>(h.p2p_cap * 2, (int64_t)(hc->n_p2p * 3 / 2) + 1024);
+        if (hc->overflow & kOvM2L)
+            h.m2l_cap = round32(std::max<int64_t>(h.m2l_cap * 2, (int64_t)hc->reg_max[0] * 5 / 4 + 256));
+        if (hc->overflow & kOvP2P)
+            h.p2p_cap = round32(std::max<int64_t>(h.p2p_cap * 2, (int64_t)hc->reg_max[1] * 5 / 4 + 256));
         if (hc->overflow & kOvNext) h.front_cap = std::max<int64_t>(h.front_cap * 2, (int64_t)(max_round * 3 / 2) + 4096);
+        if (h.m2l_cap > 0x7fffffe0ll || h.p2p_cap > 0x7fffffe0ll) {
+            set_error("dual tree traversal: list region capacity above 2^31");
+            return FMM_ERR_CAPACITY;
+        }
     }
     phase_end(h, FMM_PHASE_TRAVERSE);
 
     phase_begin(h, FMM_PHASE_LISTS);
-    FMM_TRY(group_list(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off, 1u));
-    FMM_TRY(group_list(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off, 2u));
+    const RegionList lm2l = {h.m2l_raw.as<int2>(), reg, (unsigned)h.m2l_cap, nreg};
+    const RegionList lp2p = {h.p2p_raw.as<int2>(), reg + nreg, (unsigned)h.p2p_cap, nreg};
+    FMM_TRY(group_list(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off, 1u));
+    FMM_TRY(group_list(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off, 2u));
     // P2P particle pairs (for the counters)
     FMM_CUDA(cudaMemsetAsync(&ctr->p2p_pairs, 0, sizeof(unsigned long long), h.stream));
     if (h.n_p2p > 0) {
         ++h.launches;
-        k_p2p_pairs<<<std::min(ceil_div(h.n_p2p, 256), h.num_sms * 8), 256, 0, h.stream>>>(
-            h.p2p_raw.as<int2>(), h.n_p2p, h.c_pcnt.as<int>(), &ctr->p2p_pairs);
+        k_p2p_pairs<<<nreg, 256, 0, h.stream>>>(lp2p, h.c_pcnt.as<int>(), &ctr->p2p_pairs);
     }
     FMM_CHECK_LAUNCH("p2p pairs");
     FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
@@ -613,8 +803,8 @@ int build_lists(Handle &h)
     h.nleaves = hc->nleaves;
     if (hc->seg_long) {
         // a repeated (target, source) pair: regroup that list by radix sort
-        if (hc->seg_long & 1u) FMM_TRY(group_list_radix(h, h.m2l_raw.as<int2>(), h.n_m2l, h.m2l_src, h.m2l_off));
-        if (hc->seg_long & 2u) FMM_TRY(group_list_radix(h, h.p2p_raw.as<int2>(), h.n_p2p, h.p2p_src, h.p2p_off));
+        if (hc->seg_long & 1u) FMM_TRY(group_list_radix(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off));
+        if (hc->seg_long & 2u) FMM_TRY(group_list_radix(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off));
     }
     phase_end(h, FMM_PHASE_LISTS);
     return FMM_OK;

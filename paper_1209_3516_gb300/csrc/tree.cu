@@ -101,46 +101,73 @@ __global__ void k_bbox_final(const double *part, int nb, double *norm)
         h = __dmul_rn(h, 1.0 + 0x1p-20);
         if (h == 0.0) h = 1.0;
         norm[3] = h;
+        norm[4] = __drcp_rn(h);
     }
 }
 
 // ---------------------------------------------------------------------------
 // 2. Morton keys
 // ---------------------------------------------------------------------------
+// RN(d / h) for h > 0, given y = RN(1 / h).  The estimate q0 = RN(d y) is
+// refined once with its remainder (Markstein, IBM J. Res. Develop. 34 (1990)),
+// q1 = RN(q0 + (d - q0 h) y), and then proved: |d - q1 h| < h ulp(q1) / 2
+// (tested with a 2^-20 margin, which also covers a rounded remainder) means
+// that q1 is the double nearest to d / h when q1 is normal and not a power of
+// two.  Otherwise the IEEE division decides.  The result is always RN(d / h).
+__device__ __forceinline__ double div_rn_checked(double d, double h, double y)
+{
+    const double q0 = __dmul_rn(d, y);
+    const double q1 = __fma_rn(__fma_rn(-q0, h, d), y, q0);
+    const double r = __fma_rn(-q1, h, d);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(q1) & 0x7fffffffffffffffull;
+    const int e = (int)(bits >> 52);
+    if (e >= 54 && e < 2047 && (bits & 0xfffffffffffffull) != 0ull) {
+        const double half_ulp = __longlong_as_double((long long)(e - 53) << 52);   // ulp(q1) / 2
+        if (fabs(r) < __dmul_rn(__dmul_rn(half_ulp, h), 1.0 - 0x1p-20)) return q1;
+    }
+    return __ddiv_rn(d, h);
+}
+
+// u = (x - c) / h (FP64, correctly rounded), key = interleaved floor((u + 1) 2^20)
+// per axis (clamped to 21 bits), u kept in FP64 (structure of arrays) and FP32.
 __global__ void k_morton(const double *x, int64_t n, const double *norm, uint64_t *keys, unsigned *idx,
-                         float4 *pos)
+                         float4 *pos, double *u64)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double h = norm[3];
+    const double h = norm[3], y = norm[4];
     double u[3];
     uint64_t ic[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        u[a] = __ddiv_rn(__dsub_rn(x[3 * i + a], norm[a]), h);
-        double s = floor(__dmul_rn(__dadd_rn(u[a], 1.0), 0x1p20));
-        s = fmin(fmax(s, 0.0), 2097151.0);
-        ic[a] = (uint64_t)s;
+        u[a] = div_rn_checked(__dsub_rn(x[3 * i + a], norm[a]), h, y);
+        // RN((u + 1) 2^20) in one rounding, floored and clamped in integers
+        const long long s = __double2ll_rd(__fma_rn(u[a], 0x1p20, 0x1p20));
+        ic[a] = (uint64_t)min(max(s, 0ll), 2097151ll);
+        u64[a * n + i] = u[a];
     }
     keys[i] = spread3(ic[0]) | (spread3(ic[1]) << 1) | (spread3(ic[2]) << 2);
     idx[i] = (unsigned)i;
     pos[i] = make_float4(__double2float_rn(u[0]), __double2float_rn(u[1]), __double2float_rn(u[2]), 0.0f);
 }
 
-__global__ void k_gather_sorted(const unsigned *idx, int64_t n, const float4 *pos_in, float4 *pos, int *perm)
+__global__ void k_gather_sorted(const unsigned *idx, int64_t n, const float4 *pos_in, float4 *pos, int *perm,
+                                const double *u_in, double *u_out)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const unsigned i = idx[s];
     pos[s] = pos_in[i];
     perm[s] = (int)i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u_out[a * n + s] = u_in[a * n + i];
 }
 
 int build_keys(Handle &h, const double *x)
 {
     const int64_t N = h.N;
     const int nb = std::min<int64_t>(ceil_div(N, kBBoxThreads), (int64_t)h.num_sms * 8);
-    FMM_TRY(h.norm.reserve(4 * sizeof(double)));
+    FMM_TRY(h.norm.reserve(5 * sizeof(double)));   // centre, h, RN(1 / h)
     FMM_TRY(h.bbox_part.reserve((size_t)nb * 6 * sizeof(double)));
     FMM_TRY(h.err_flag.reserve(sizeof(unsigned)));
     FMM_TRY(h.keys.reserve(N * sizeof(uint64_t)));
@@ -148,6 +175,8 @@ int build_keys(Handle &h, const double *x)
     FMM_TRY(h.idx.reserve(N * sizeof(unsigned)));
     FMM_TRY(h.idx_alt.reserve(N * sizeof(unsigned)));
     FMM_TRY(h.pos_unsorted.reserve(N * sizeof(float4)));
+    FMM_TRY(h.u_unsorted.reserve(3 * N * sizeof(double)));
+    FMM_TRY(h.u_sorted.reserve(3 * N * sizeof(double)));
     FMM_TRY(h.pos.reserve(N * sizeof(float4)));
     FMM_TRY(h.perm.reserve(N * sizeof(int)));
 
@@ -159,7 +188,8 @@ int build_keys(Handle &h, const double *x)
     k_bbox_final<<<1, 256, 0, h.stream>>>(h.bbox_part.as<double>(), nb, h.norm.as<double>());
     ++h.launches;
     k_morton<<<ceil_div(N, 256), 256, 0, h.stream>>>(x, N, h.norm.as<double>(), h.keys.as<uint64_t>(),
-                                                     h.idx.as<unsigned>(), h.pos_unsorted.as<float4>());
+                                                     h.idx.as<unsigned>(), h.pos_unsorted.as<float4>(),
+                                                     h.u_unsorted.as<double>());
     FMM_CHECK_LAUNCH("morton");
     phase_end(h, FMM_PHASE_MORTON);
 
@@ -183,7 +213,8 @@ int build_keys(Handle &h, const double *x)
     }
     ++h.launches;
     k_gather_sorted<<<ceil_div(N, 256), 256, 0, h.stream>>>(h.idx.as<unsigned>(), N, h.pos_unsorted.as<float4>(),
-                                                            h.pos.as<float4>(), h.perm.as<int>());
+                                                            h.pos.as<float4>(), h.perm.as<int>(),
+                                                            h.u_unsorted.as<double>(), h.u_sorted.as<double>());
     FMM_CHECK_LAUNCH("gather");
     phase_end(h, FMM_PHASE_SORT);
     return FMM_OK;
@@ -381,26 +412,21 @@ __global__ void k_radius_final(int nc, const unsigned *r2bits, float4 *geom)
 
 // Particle positions are stored as FP32 offsets from the centre of their
 // leaf's parent (the "frame" cell; the root frames itself), d = u - X_frame,
-// rounded once from FP64 (u recomputed exactly as for the keys).  Cell centres
-// are exact in FP32, so kernels recover differences of nearby particles to
-// ~2^-24 of the frame size instead of 2^-24 of the domain size; sibling leaves
-// share a frame, so a run of consecutive siblings is one contiguous block of
-// particles in one frame.
-__global__ void k_local_positions(const double *x, int64_t n, const int *perm, const double *norm, const int *leaf_of,
-                                  const int *parent, const float4 *geom, float4 *pos)
+// rounded once from the FP64 coordinates u of the key computation.  Cell
+// centres are exact in FP32, so kernels recover differences of nearby
+// particles to ~2^-24 of the frame size instead of 2^-24 of the domain size;
+// sibling leaves share a frame, so a run of consecutive siblings is one
+// contiguous block of particles in one frame.
+__global__ void k_local_positions(int64_t n, const double *u, const int *leaf_of, const int *parent,
+                                  const float4 *geom, float4 *pos)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const int64_t i = perm[s];
-    const double h = norm[3];
     const int lf = leaf_of[s];
     const int fr = parent[lf] >= 0 ? parent[lf] : lf;
     const float4 X = geom[fr];
-    const double cx = X.x, cy = X.y, cz = X.z;
-    const double ux = __ddiv_rn(__dsub_rn(x[3 * i + 0], norm[0]), h);
-    const double uy = __ddiv_rn(__dsub_rn(x[3 * i + 1], norm[1]), h);
-    const double uz = __ddiv_rn(__dsub_rn(x[3 * i + 2], norm[2]), h);
-    pos[s] = make_float4(__double2float_rn(ux - cx), __double2float_rn(uy - cy), __double2float_rn(uz - cz), 0.0f);
+    pos[s] = make_float4(__double2float_rn(u[s] - (double)X.x), __double2float_rn(u[n + s] - (double)X.y),
+                         __double2float_rn(u[2 * n + s] - (double)X.z), 0.0f);
 }
 
 static int grow_cells(Handle &h, int64_t need)
@@ -484,9 +510,9 @@ int build_tree(Handle &h, const double *x)
     k_radius_final<<<ceil_div(nc, 256), 256, 0, h.stream>>>(nc, h.c_r2bits.as<unsigned>(), h.c_geom.as<float4>());
     // from here on particles are stored relative to the centre of their leaf's parent
     ++h.launches;
-    k_local_positions<<<ceil_div(N, 256), 256, 0, h.stream>>>(x, N, h.perm.as<int>(), h.norm.as<double>(),
-                                                              h.leaf_of.as<int>(), h.c_parent.as<int>(),
-                                                              h.c_geom.as<float4>(), h.pos.as<float4>());
+    k_local_positions<<<ceil_div(N, 256), 256, 0, h.stream>>>(N, h.u_sorted.as<double>(), h.leaf_of.as<int>(),
+                                                              h.c_parent.as<int>(), h.c_geom.as<float4>(),
+                                                              h.pos.as<float4>());
     FMM_CHECK_LAUNCH("geometry");
     phase_end(h, FMM_PHASE_TREE);
     return FMM_OK;
