@@ -92,7 +92,8 @@ struct DeviceGuard {
     }
 };
 
-// Errors that kernels record asynchronously (bit 1 of err_flag: a bounded wait of
+// Errors that kernels record asynchronously (bit 3 of err_flag, a radix-sort
+// look-back wait, is checked at the end of every build; bit 1: a bounded wait of
 // the P2P staging gave up); read at the synchronising entry points.
 static int check_async_errors(Handle &h)
 {
@@ -127,7 +128,13 @@ static int do_build(Handle &h, const double *x)
     FMM_TRY(build_p2p_items(h));
     phase_end(h, FMM_PHASE_ITEMS);
     if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
+    FMM_CUDA(cudaMemcpyAsync(&h.pinned->err, h.err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
     FMM_CUDA(cudaStreamSynchronize(h.stream));
+    if (h.pinned->err & 8u) {
+        FMM_CUDA(cudaMemsetAsync(h.err_flag.p, 0, sizeof(unsigned), h.stream));
+        set_error("fmm_build: a radix-sort look-back wait gave up; the build is invalid");
+        return FMM_ERR_CUDA;
+    }
     if (h.events_ready) cudaEventElapsedTime(&h.ms_build, h.ev[ev0], h.ev[ev1]);
     h.x_built = x;
     h.built = true;

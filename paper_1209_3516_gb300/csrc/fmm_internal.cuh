@@ -108,7 +108,7 @@ struct Handle {
     // normalisation / keys / sort
     DevBuf norm;          // double[4] + bbox partials
     DevBuf bbox_part;     // double[nblocks * 6]
-    DevBuf err_flag;      // unsigned int: bit 0 = non-finite input
+    DevBuf err_flag;      // unsigned int: bit 0 = non-finite input, 1 = P2P staging wait, 2 = tensor-core wait, 3 = radix look-back wait
     DevBuf keys, keys_alt;        // u64[N]
     DevBuf idx, idx_alt;          // u32[N]
     DevBuf sort_hist;             // u32[256 * tiles]

@@ -257,6 +257,154 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *keys, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// One-sweep LSD radix sort (one kernel per 8-bit pass): the digit totals of
+// every pass come from one histogram kernel; in a pass, each block claims the
+// next tile in order, ranks its keys stably per warp (__match_any_sync peer
+// groups, warp-private running counts), publishes the tile's digit counts and
+// finds the count of each digit in all earlier tiles by looking back over
+// their published counts (decoupled look-back: a tile whose prefix is known
+// publishes the inclusive prefix, so a look-back stops there), then scatters.
+// Every wait of the look-back is bounded; a wait that gives up sets bit 8 of
+// the error word (the build then fails instead of hanging).
+// ---------------------------------------------------------------------------
+constexpr int kOsThreads = 512;                         // threads 0..255 also own one digit each
+constexpr int kOsWarps = kOsThreads / 32;
+constexpr int kOsPerThread = 8;                         // keys per thread
+constexpr int kOsTile = kOsThreads * kOsPerThread;      // 4096 keys per tile
+constexpr unsigned kOsAgg = 1u << 30, kOsPrefix = 2u << 30, kOsValue = (1u << 30) - 1u;
+constexpr int kOsSpinMax = 1 << 20;   // look-back windows without progress before giving up
+constexpr int kOsWindow = 16;          // predecessors read per look-back window
+
+// A status word holds its own flag and count in one 32-bit store, and nothing
+// else is read through it, so relaxed device-scope accesses suffice.
+__device__ __forceinline__ void st_status(unsigned *p, unsigned v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_status(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ghist[pass][digit] += count of keys with that digit, for every pass.
+template <class K>
+__global__ void __launch_bounds__(kOsThreads) k_os_hist(const K *keys, int64_t n, int begin_bit, int npass,
+                                                        unsigned *ghist)
+{
+    __shared__ unsigned h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const K k = keys[i];
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(unsigned)(k >> (begin_bit + 8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
+        const unsigned c = (&h[0][0])[i];
+        if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+template <class K, bool kVals>
+__global__ void __launch_bounds__(kOsThreads, 2) k_os_pass(const K *keys, const unsigned *vals, int64_t n, int shift,
+                                                        const unsigned *ghist, unsigned *status, unsigned *tile_ctr,
+                                                        K *keys_out, unsigned *vals_out, unsigned *err)
+{
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_wcnt[kOsWarps][256];   // per-warp running digit counts, then warp offsets
+    __shared__ unsigned s_base[256];             // global position of the tile's first key of each digit
+    const unsigned t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int i = t; i < kOsWarps * 256; i += kOsThreads) (&s_wcnt[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned tile = s_tile;
+    // digit start over all keys (exclusive scan of this pass's totals)
+    const unsigned dstart = block_exclusive_scan(t < 256u ? ghist[t] : 0u, nullptr);
+    // warp w ranks its keys [w 32 R, (w + 1) 32 R) of the tile, 32 per round in order
+    const int64_t base = (int64_t)tile * kOsTile + (int64_t)warp * 32 * kOsPerThread;
+    K key[kOsPerThread];
+    unsigned val[kOsPerThread], dig[kOsPerThread], rank[kOsPerThread];
+#pragma unroll
+    for (int r = 0; r < kOsPerThread; ++r) {
+        const int64_t i = base + 32 * r + lane;
+        const bool valid = i < n;
+        key[r] = valid ? keys[i] : (K)0;
+        val[r] = (kVals && valid) ? vals[i] : 0u;
+        dig[r] = valid ? ((unsigned)(key[r] >> shift) & 0xffu) : 256u;
+    }
+#pragma unroll
+    for (int r = 0; r < kOsPerThread; ++r) {
+        const unsigned d = dig[r];
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned before = d < 256u ? s_wcnt[warp][d] : 0u;
+        rank[r] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (d < 256u && lane == (unsigned)(__ffs(peers) - 1)) s_wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t < 256 = digit t: the tile's count and each warp's offset within
+    // the tile, then the count in all earlier tiles
+    if (t < 256u) {
+    unsigned cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kOsWarps; ++w) {
+        const unsigned c = s_wcnt[w][t];
+        s_wcnt[w][t] = cnt;
+        cnt += c;
+    }
+    // publish, then look back for the count of digit t in all earlier tiles
+    unsigned *st = status + (size_t)tile * 256;
+    unsigned excl = 0;
+    if (tile == 0) {
+        st_status(st + t, kOsPrefix | cnt);
+    } else {
+        st_status(st + t, kOsAgg | cnt);
+        // windows of kOsWindow predecessors: their words are read together, then
+        // consumed nearest first up to the first word not yet published (read
+        // again in the next window) or the first inclusive prefix
+        int64_t j = (int64_t)tile - 1;
+        int idle = 0;
+        for (;;) {
+            unsigned v[kOsWindow];
+#pragma unroll
+            for (int q = 0; q < kOsWindow; ++q)
+                v[q] = j - q >= 0 ? ld_status(status + (size_t)(j - q) * 256 + t) : kOsPrefix;
+            int used = 0;
+            bool found = false;
+#pragma unroll
+            for (int q = 0; q < kOsWindow; ++q) {
+                if (found || used < q || !(v[q] & (kOsAgg | kOsPrefix))) continue;
+                excl += v[q] & kOsValue;
+                used = q + 1;
+                found = (v[q] & kOsPrefix) != 0;
+            }
+            if (found) break;
+            j -= used;
+            if (used == 0 && ++idle >= kOsSpinMax) {
+                atomicOr(err, 8u);
+                break;
+            }
+        }
+        st_status(st + t, kOsPrefix | (excl + cnt));
+    }
+    s_base[t] = dstart + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kOsPerThread; ++r) {
+        const unsigned d = dig[r];
+        if (d < 256u) {
+            const unsigned pos = s_base[d] + s_wcnt[warp][d] + rank[r];
+            keys_out[pos] = key[r];
+            if (kVals) vals_out[pos] = val[r];
+        }
+    }
+}
+
 template <class K>
 static int radix_sort_impl(Handle &h, K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_alt, bool with_vals,
                            int64_t n, int begin_bit, int end_bit)
@@ -265,6 +413,38 @@ static int radix_sort_impl(Handle &h, K *&keys, K *&keys_alt, unsigned *&vals, u
     if (n > 0xffffffffll) {
         set_error("radix sort: more than 2^32 keys");
         return FMM_ERR_ARG;
+    }
+    const int npass = (end_bit - begin_bit + 7) / 8;
+    if (n < (int64_t)kOsValue && npass <= 8) {
+        // one-sweep passes
+        const int ntiles = ceil_div(n, (int64_t)kOsTile);
+        const size_t words = (size_t)npass * 256 + (size_t)npass * 32 + (size_t)npass * ntiles * 256;
+        FMM_TRY(h.sort_hist.reserve(words * sizeof(unsigned)));
+        FMM_TRY(h.err_flag.reserve(sizeof(unsigned)));
+        unsigned *ghist = h.sort_hist.as<unsigned>();
+        unsigned *ctrs = ghist + (size_t)npass * 256;   // one tile counter per pass (32-word stride)
+        unsigned *status = ctrs + (size_t)npass * 32;
+        FMM_CUDA(cudaMemsetAsync(ghist, 0, words * sizeof(unsigned), h.stream));
+        ++h.launches;
+        k_os_hist<K><<<std::min<int64_t>(ceil_div(n, (int64_t)kOsThreads * 8), (int64_t)h.num_sms * 8), kOsThreads,
+                       0, h.stream>>>(keys, n, begin_bit, npass, ghist);
+        for (int p = 0; p < npass; ++p) {
+            const int shift = begin_bit + 8 * p;
+            unsigned *stp = status + (size_t)p * ntiles * 256;
+            ++h.launches;
+            if (with_vals)
+                k_os_pass<K, true><<<ntiles, kOsThreads, 0, h.stream>>>(keys, vals, n, shift, ghist + 256 * p, stp,
+                                                                       ctrs + 32 * p, keys_alt, vals_alt,
+                                                                       h.err_flag.as<unsigned>());
+            else
+                k_os_pass<K, false><<<ntiles, kOsThreads, 0, h.stream>>>(keys, nullptr, n, shift, ghist + 256 * p,
+                                                                        stp, ctrs + 32 * p, keys_alt, nullptr,
+                                                                        h.err_flag.as<unsigned>());
+            FMM_CHECK_LAUNCH("radix pass");
+            std::swap(keys, keys_alt);
+            if (with_vals) std::swap(vals, vals_alt);
+        }
+        return FMM_OK;
     }
     // tiles small enough that the grid covers the SMs about four times over
     // (latency-bound kernels), at most 16 rounds of 256 keys
