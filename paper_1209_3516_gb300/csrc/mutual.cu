@@ -154,15 +154,29 @@ int build_mutual(Handle &h)
 // ---------------------------------------------------------------------------
 constexpr int kMuG = 16;           // targets per work item (the P2P items)
 constexpr int kMuThreads = 64;     // two warps per block
-constexpr int kMuSlots = 256;      // staged sources per buffer
-constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots * (int)sizeof(float4));
+#ifndef FMM_MU_SLOTS
+#define FMM_MU_SLOTS 256
+#endif
+constexpr int kMuSlots = FMM_MU_SLOTS;   // staged sources per buffer
+constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots + kMuG) * (int)sizeof(float4);
 #ifndef FMM_MU_PER_LANE
-#define FMM_MU_PER_LANE 4
+#define FMM_MU_PER_LANE 2
 #endif
 constexpr int kMuPerLane = FMM_MU_PER_LANE;   // staged sources per lane per step
 #ifndef FMM_MU_MIN_BLOCKS
-#define FMM_MU_MIN_BLOCKS 4
+#define FMM_MU_MIN_BLOCKS 6
 #endif
+#ifndef FMM_MU_TARGETS_SMEM
+#define FMM_MU_TARGETS_SMEM 1
+#endif
+// 1: the item's targets sit in shared memory (read by broadcast), so that the
+// kernel fits 168 registers and 6 blocks (12 warps) per SM; 0: in registers
+// (244 registers, 4 blocks per SM).  N = 1M, P = 8, theta = 0.5, mutual pass:
+// registers / 4 blocks / 4 sources per lane 5.03 ms; shared / 6 / 2: 4.74 ms;
+// shared / 6 / 3 (166 registers) 5.14; shared / 7-8 blocks with 192 staged
+// sources per buffer (spills) 5.00-5.08.
+constexpr bool kMuTargetsSmem = FMM_MU_TARGETS_SMEM != 0;
+constexpr int kMuTargetF4 = kMuG;   // per warp: (ntx, nty) and (ntz, nqt) float4 of each target pair
 
 __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c, float d)
 {
@@ -204,20 +218,33 @@ __device__ __forceinline__ int mu_stage(RunCursor &cur, const float4 *run, const
 // positions, nqt negated target charges; acc[4h + k] the target side, ps, gs
 // the sources' reactions (ps accumulates -phi_s).
 template <int NT, int U>
-__device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx, const float2 *nty, const float2 *ntz,
-                                        const float2 *nqt, float2 *acc, float2 *ps, float2 *gsx, float2 *gsy,
-                                        float2 *gsz)
+__device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx_r, const float2 *nty_r,
+                                        const float2 *ntz_r, const float2 *nqt_r, const float4 *tsm, float2 *acc,
+                                        float2 *ps, float2 *gsx, float2 *gsy, float2 *gsz)
 {
     constexpr float kEps = 1.17549435e-38f;
     const float2 eps = make_float2(kEps, kEps);
 #pragma unroll
     for (int h = 0; h < NT / 2; ++h) {
+        float2 ntx[1], nty[1], ntz[1], nqt[1];
+        if constexpr (kMuTargetsSmem) {
+            const float4 a = tsm[2 * h], b = tsm[2 * h + 1];
+            ntx[0] = make_float2(a.x, a.y);
+            nty[0] = make_float2(a.z, a.w);
+            ntz[0] = make_float2(b.x, b.y);
+            nqt[0] = make_float2(b.z, b.w);
+        } else {
+            ntx[0] = ntx_r[h];
+            nty[0] = nty_r[h];
+            ntz[0] = ntz_r[h];
+            nqt[0] = nqt_r[h];
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const float2 sq = make_float2(s[u].w, s[u].w);
-            const float2 dx = __fadd2_rn(make_float2(s[u].x, s[u].x), ntx[h]);
-            const float2 dy = __fadd2_rn(make_float2(s[u].y, s[u].y), nty[h]);
-            const float2 dz = __fadd2_rn(make_float2(s[u].z, s[u].z), ntz[h]);
+            const float2 dx = __fadd2_rn(make_float2(s[u].x, s[u].x), ntx[0]);
+            const float2 dy = __fadd2_rn(make_float2(s[u].y, s[u].y), nty[0]);
+            const float2 dz = __fadd2_rn(make_float2(s[u].z, s[u].z), ntz[0]);
             float2 r2 = __ffma2_rn(dx, dx, eps);
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
@@ -230,8 +257,8 @@ __device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx, cons
             acc[4 * h + 2] = __ffma2_rn(qs3, dy, acc[4 * h + 2]);
             acc[4 * h + 3] = __ffma2_rn(qs3, dz, acc[4 * h + 3]);
             // reaction: -phi_s += (-q_t) / r, grad_s += (-q_t) e / r^3
-            ps[u] = __ffma2_rn(nqt[h], rinv, ps[u]);
-            const float2 qt3 = __fmul2_rn(nqt[h], rinv3);
+            ps[u] = __ffma2_rn(nqt[0], rinv, ps[u]);
+            const float2 qt3 = __fmul2_rn(nqt[0], rinv3);
             gsx[u] = __ffma2_rn(qt3, dx, gsx[u]);
             gsy[u] = __ffma2_rn(qt3, dy, gsy[u]);
             gsz[u] = __ffma2_rn(qt3, dz, gsz[u]);
@@ -242,7 +269,7 @@ __device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx, cons
 template <int NT>
 __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
                                           float4 *buf, const float2 *ntx, const float2 *nty, const float2 *ntz,
-                                          const float2 *nqt, float2 *acc, float4 *racc)
+                                          const float2 *nqt, const float4 *tsm, float2 *acc, float4 *racc)
 {
     const int lane = (int)lane_id();
     int n_cur = mu_stage(cur, run, run_end, pos, buf, buf + kMuSlots);
@@ -276,7 +303,7 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
                 }
                 ps[u] = gsx[u] = gsy[u] = gsz[u] = make_float2(0.f, 0.f);
             }
-            mu_tile<NT, kMuPerLane>(s, ntx, nty, ntz, nqt, acc, ps, gsx, gsy, gsz);
+            mu_tile<NT, kMuPerLane>(s, ntx, nty, ntz, nqt, tsm, acc, ps, gsx, gsy, gsz);
 #pragma unroll
             for (int u = 0; u < kMuPerLane; ++u)
                 if (sidx[u] >= 0)
@@ -297,7 +324,8 @@ __global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
     const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= nitems) return;
     const unsigned lane = lane_id();
-    float4 *buf = mu_smem + (threadIdx.x >> 5) * (4 * kMuSlots);
+    float4 *buf = mu_smem + (threadIdx.x >> 5) * (4 * kMuSlots + kMuG);
+    float4 *tsm = buf + 4 * kMuSlots;   // the targets (shared-memory form)
     const int4 it = items[item];
     const int tb = it.y, tc = it.z;
     RunCursor cur;
@@ -305,24 +333,36 @@ __global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
     if (cur.e >= cur.e1) return;   // no mutual sources
     // targets (negated positions and charges, float2 pairs); slots past the
     // count repeat the last target's position with charge 0 (no reaction)
-    float2 ntx[kMuG / 2], nty[kMuG / 2], ntz[kMuG / 2], nqt[kMuG / 2];
+    float2 ntx[kMuTargetsSmem ? 1 : kMuG / 2], nty[kMuTargetsSmem ? 1 : kMuG / 2],
+        ntz[kMuTargetsSmem ? 1 : kMuG / 2], nqt[kMuTargetsSmem ? 1 : kMuG / 2];
+    if constexpr (kMuTargetsSmem) {
+        if (lane < (unsigned)(kMuG / 2)) {
+            const int h = (int)lane;
+            const float4 p0 = pos[tb + min(2 * h, tc - 1)];
+            const float4 p1 = pos[tb + min(2 * h + 1, tc - 1)];
+            tsm[2 * h] = make_float4(-p0.x, -p1.x, -p0.y, -p1.y);
+            tsm[2 * h + 1] = make_float4(-p0.z, -p1.z, 2 * h < tc ? -p0.w : 0.0f, 2 * h + 1 < tc ? -p1.w : 0.0f);
+        }
+        __syncwarp();
+    } else {
 #pragma unroll
-    for (int h = 0; h < kMuG / 2; ++h) {
-        const float4 p0 = pos[tb + min(2 * h, tc - 1)];
-        const float4 p1 = pos[tb + min(2 * h + 1, tc - 1)];
-        ntx[h] = make_float2(-p0.x, -p1.x);
-        nty[h] = make_float2(-p0.y, -p1.y);
-        ntz[h] = make_float2(-p0.z, -p1.z);
-        nqt[h] = make_float2(2 * h < tc ? -p0.w : 0.0f, 2 * h + 1 < tc ? -p1.w : 0.0f);
+        for (int h = 0; h < kMuG / 2; ++h) {
+            const float4 p0 = pos[tb + min(2 * h, tc - 1)];
+            const float4 p1 = pos[tb + min(2 * h + 1, tc - 1)];
+            ntx[h] = make_float2(-p0.x, -p1.x);
+            nty[h] = make_float2(-p0.y, -p1.y);
+            ntz[h] = make_float2(-p0.z, -p1.z);
+            nqt[h] = make_float2(2 * h < tc ? -p0.w : 0.0f, 2 * h + 1 < tc ? -p1.w : 0.0f);
+        }
     }
     float2 a[2 * kMuG];
 #pragma unroll
     for (int i = 0; i < 2 * kMuG; ++i) a[i] = make_float2(0.0f, 0.0f);
     const int ntr = tc <= 4 ? 4 : tc <= 8 ? 8 : tc <= 12 ? 12 : 16;
-    if (ntr == 4) mu_stream<4>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
-    else if (ntr == 8) mu_stream<8>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
-    else if (ntr == 12) mu_stream<12>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
-    else mu_stream<16>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, a, racc);
+    if (ntr == 4) mu_stream<4>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else if (ntr == 8) mu_stream<8>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else if (ntr == 12) mu_stream<12>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else mu_stream<16>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
     // target side: reduce-scatter, lanes 2g / 2g + 1 add (phi, gx) / (gy, gz) of target g
     float v[64];
 #pragma unroll

@@ -418,16 +418,6 @@ template <class F> __device__ __forceinline__ void for_each_chunk(const RegionLi
     }
 }
 
-__global__ void k_p2p_pairs(RegionList L, const int *pcnt, unsigned long long *total)
-{
-    unsigned long long s = 0;
-    for_each_chunk(L, [&](int2 p, bool valid, int, unsigned) {
-        if (valid) s += (unsigned long long)pcnt[p.x] * (unsigned long long)pcnt[p.y];
-    });
-    s = warp_sum(s);
-    if (lane_id() == 0 && s) atomicAdd(total, s);
-}
-
 // dense[roff[r] + k] = pair k of region r
 __global__ void k_compact_regions(RegionList L, const unsigned *roff, int2 *dense)
 {
@@ -492,13 +482,20 @@ constexpr int kSegWords = 1024;                  // bitmap words per warp
 constexpr int kSegBits = 32 * kSegWords;         // source indices per window
 constexpr int kSegPhys = kSegWords + kSegWords / 32;   // skewed: word j at j + j / 32
 
-__global__ void k_list_count(RegionList L, unsigned *cnt)
+// With pcnt (the P2P list), also the particle-pair total sum n_T n_S.
+__global__ void k_list_count(RegionList L, unsigned *cnt, const int *pcnt, unsigned long long *pairs_total)
 {
     const int lane = (int)lane_id();
-    for_each_chunk(L, [&](int2 p, bool, int, unsigned) {
+    unsigned long long np = 0;
+    for_each_chunk(L, [&](int2 p, bool valid, int, unsigned) {
         const unsigned peers = __match_any_sync(kFull, p.x);
         if (p.x >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[p.x], (unsigned)__popc(peers));
+        if (pcnt && valid) np += (unsigned long long)pcnt[p.x] * (unsigned long long)pcnt[p.y];
     });
+    if (pcnt) {
+        np = warp_sum(np);
+        if (lane == 0 && np) atomicAdd(pairs_total, np);
+    }
 }
 
 // tmp[off[t] + slot] = s for every pair (t, s); the slots of a target are
@@ -595,7 +592,8 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_list_segsort(int nc, const u
 // are the sources of target c, ascending.  A repeated (target, source) pair
 // sets `bit` in ctr->seg_long (read at the end of the list phase, which then
 // regroups that list with the radix form).
-static int group_list(Handle &h, const RegionList &L, int64_t n, DevBuf &src, DevBuf &off, unsigned bit)
+static int group_list(Handle &h, const RegionList &L, int64_t n, DevBuf &src, DevBuf &off, unsigned bit,
+                      const int *pcnt = nullptr, unsigned long long *pairs_total = nullptr)
 {
     const int nc = (int)h.ncells;
     FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
@@ -608,7 +606,7 @@ static int group_list(Handle &h, const RegionList &L, int64_t n, DevBuf &src, De
     const int gb = L.nreg;   // one block per region
     if (n > 0) {
         ++h.launches;
-        k_list_count<<<gb, 256, 0, h.stream>>>(L, cnt);
+        k_list_count<<<gb, 256, 0, h.stream>>>(L, cnt, pcnt, pairs_total);
     }
     FMM_TRY(scan_exclusive_u32(h, cnt, offu, nc + 1, nullptr));
     if (n > 0) {
@@ -788,15 +786,10 @@ int build_lists(Handle &h)
     phase_begin(h, FMM_PHASE_LISTS);
     const RegionList lm2l = {h.m2l_raw.as<int2>(), reg, (unsigned)h.m2l_cap, nreg};
     const RegionList lp2p = {h.p2p_raw.as<int2>(), reg + nreg, (unsigned)h.p2p_cap, nreg};
-    FMM_TRY(group_list(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off, 1u));
-    FMM_TRY(group_list(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off, 2u));
-    // P2P particle pairs (for the counters)
+    // the P2P particle-pair total (for the counters) comes with the P2P list's counts
     FMM_CUDA(cudaMemsetAsync(&ctr->p2p_pairs, 0, sizeof(unsigned long long), h.stream));
-    if (h.n_p2p > 0) {
-        ++h.launches;
-        k_p2p_pairs<<<nreg, 256, 0, h.stream>>>(lp2p, h.c_pcnt.as<int>(), &ctr->p2p_pairs);
-    }
-    FMM_CHECK_LAUNCH("p2p pairs");
+    FMM_TRY(group_list(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off, 1u));
+    FMM_TRY(group_list(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off, 2u, h.c_pcnt.as<int>(), &ctr->p2p_pairs));
     FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
     FMM_CUDA(cudaStreamSynchronize(h.stream));
     h.p2p_pairs = (int64_t)hc->p2p_pairs;
