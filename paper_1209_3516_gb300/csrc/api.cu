@@ -115,6 +115,11 @@ static int check_async_errors(Handle &h)
 
 static int do_build(Handle &h, const double *x)
 {
+    if (h.side_pending) {
+        // a build that failed after forking the M2L grouping: let it finish
+        h.side_pending = false;
+        FMM_CUDA(cudaStreamSynchronize(h.side));
+    }
     h.built = false;
     h.evaluated = false;
     h.backward_done = false;
@@ -127,9 +132,11 @@ static int do_build(Handle &h, const double *x)
     phase_begin(h, FMM_PHASE_ITEMS);
     FMM_TRY(build_p2p_items(h));
     phase_end(h, FMM_PHASE_ITEMS);
+    FMM_TRY(join_lists_begin(h));
     if (h.events_ready) cudaEventRecord(h.ev[ev1], h.stream);
     FMM_CUDA(cudaMemcpyAsync(&h.pinned->err, h.err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, h.stream));
     FMM_CUDA(cudaStreamSynchronize(h.stream));
+    FMM_TRY(join_lists_end(h));
     if (h.pinned->err & 8u) {
         FMM_CUDA(cudaMemsetAsync(h.err_flag.p, 0, sizeof(unsigned), h.stream));
         set_error("fmm_build: a radix-sort look-back wait gave up; the build is invalid");
@@ -244,6 +251,15 @@ int fmm_destroy(fmm_handle *w)
                       &h.os_off, &h.os_src, &h.mu_cnt_tmp, &h.mu_poff, &h.mu_ent, &h.mu_cnt, &h.os_poff, &h.os_ent,
                       &h.os_cnt, &h.racc, &h.Mf};
     for (DevBuf *b : bufs) b->release();
+    h.lcnt_side.release();
+    h.lkeys_side.release();
+    h.scan_tmp_side.release();
+    if (h.side) {
+        cudaStreamSynchronize(h.side);
+        cudaStreamDestroy(h.side);
+        cudaEventDestroy(h.ev_fork);
+        cudaEventDestroy(h.ev_join);
+    }
     if (h.events_ready)
         for (auto &ev : h.ev) cudaEventDestroy(ev);
     if (h.pinned) cudaFreeHost(h.pinned);

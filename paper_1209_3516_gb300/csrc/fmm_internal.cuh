@@ -143,6 +143,12 @@ struct Handle {
     // grouped lists
     DevBuf lkeys, lkeys_alt;   // packed (target, source) keys of the radix grouping (long lists only)
     DevBuf lcnt;               // unsigned[ncells + 1]: per-target counts, then offsets, of the grouping
+    // the M2L list is grouped on a second stream, beside the P2P list and the
+    // mutual split (its own scratch; joined before the build returns)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_pending = false;
+    DevBuf lcnt_side, lkeys_side, scan_tmp_side;
     DevBuf m2l_src, m2l_off;   // int32 sources, CSR offsets (ncells + 1)
     DevBuf p2p_src, p2p_off;
     DevBuf leaf_list;          // int32 leaf cell ids
@@ -208,6 +214,8 @@ struct Handle {
 // phases (implemented in the .cu files)
 // ---------------------------------------------------------------------------
 int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, unsigned *total_dev);
+int scan_exclusive_u32_on(Handle &h, cudaStream_t stream, DevBuf &tmp, const unsigned *in, unsigned *out, int64_t n,
+                          unsigned *total_dev);
 int radix_sort_pairs(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, unsigned *&vals,
                      unsigned *&vals_alt, int64_t n, int begin_bit, int end_bit);
 int radix_sort_keys(Handle &h, uint64_t *&keys, uint64_t *&keys_alt, int64_t n, int begin_bit,
@@ -216,7 +224,9 @@ int radix_sort_keys32(Handle &h, uint32_t *&keys, uint32_t *&keys_alt, int64_t n
 
 int build_keys(Handle &h, const double *x);       // bbox, normalise, Morton, sort, gather
 int build_tree(Handle &h, const double *x);       // cells, geometry, leaf-local positions
-int build_lists(Handle &h);                       // DTT + grouping
+int build_lists(Handle &h);                       // DTT + grouping (the M2L list on the second stream)
+int join_lists_begin(Handle &h);                  // the handle's stream waits for the M2L list's grouping
+int join_lists_end(Handle &h);                    // after a synchronisation: its repeated-pair check
 int build_p2p_items(Handle &h);                   // P2P work items and source ranges
 int build_work_items(Handle &h, int g, DevBuf &items, int64_t &n_items);   // items of <= g targets
 int p2p_batch_tc(Handle &h, int nrhs, float *phi, float *grad);   // batched P2P + L2P, tensor cores

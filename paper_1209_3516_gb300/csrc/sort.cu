@@ -165,25 +165,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(const unsigned *in
 
 int scan_exclusive_u32(Handle &h, const unsigned *in, unsigned *out, int64_t n, unsigned *total_dev)
 {
+    return scan_exclusive_u32_on(h, h.stream, h.scan_tmp, in, out, n, total_dev);
+}
+
+int scan_exclusive_u32_on(Handle &h, cudaStream_t stream, DevBuf &tmp, const unsigned *in, unsigned *out, int64_t n,
+                          unsigned *total_dev)
+{
     if (n <= 0) {
-        if (total_dev) FMM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(unsigned), h.stream));
+        if (total_dev) FMM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(unsigned), stream));
         return FMM_OK;
     }
     if (n <= kScanSingleMax) {
         ++h.launches;
-        k_scan_single<<<1, kScanThreads, 0, h.stream>>>(in, n, out, total_dev);
+        k_scan_single<<<1, kScanThreads, 0, stream>>>(in, n, out, total_dev);
         FMM_CHECK_LAUNCH("scan");
         return FMM_OK;
     }
     const int nb = ceil_div(n, kScanChunk);
-    FMM_TRY(h.scan_tmp.reserve((size_t)(nb + 1) * sizeof(unsigned)));
-    unsigned *sums = h.scan_tmp.as<unsigned>();
+    FMM_TRY(tmp.reserve((size_t)(nb + 1) * sizeof(unsigned)));
+    unsigned *sums = tmp.as<unsigned>();
     ++h.launches;
-    k_scan_reduce<<<nb, kScanThreads, 0, h.stream>>>(in, n, sums);
+    k_scan_reduce<<<nb, kScanThreads, 0, stream>>>(in, n, sums);
     ++h.launches;
-    k_scan_blocks<<<1, kScanThreads, 0, h.stream>>>(sums, nb, total_dev);
+    k_scan_blocks<<<1, kScanThreads, 0, stream>>>(sums, nb, total_dev);
     ++h.launches;
-    k_scan_apply<<<nb, kScanThreads, 0, h.stream>>>(in, n, sums, out);
+    k_scan_apply<<<nb, kScanThreads, 0, stream>>>(in, n, sums, out);
     FMM_CHECK_LAUNCH("scan");
     return FMM_OK;
 }

@@ -590,33 +590,72 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_list_segsort(int nc, const u
 
 // Group the (target, source) pairs by target into CSR form: off[c] .. off[c+1]
 // are the sources of target c, ascending.  A repeated (target, source) pair
-// sets `bit` in ctr->seg_long (read at the end of the list phase, which then
-// regroups that list with the radix form).
-static int group_list(Handle &h, const RegionList &L, int64_t n, DevBuf &src, DevBuf &off, unsigned bit,
+// sets `bit` in ctr->seg_long (read once the list is complete, which then
+// regroups that list with the radix form).  Runs on `stream` with the given
+// scratch (count / offset array, unordered sources, scan blocks).
+static int group_list(Handle &h, cudaStream_t stream, DevBuf &lcnt, DevBuf &lkeys, DevBuf &scan_tmp,
+                      const RegionList &L, int64_t n, DevBuf &src, DevBuf &off, unsigned bit,
                       const int *pcnt = nullptr, unsigned long long *pairs_total = nullptr)
 {
     const int nc = (int)h.ncells;
     FMM_TRY(src.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
     FMM_TRY(off.reserve((size_t)(nc + 1) * sizeof(int)));
-    FMM_TRY(h.lcnt.reserve((size_t)(nc + 1) * sizeof(unsigned)));
-    FMM_TRY(h.lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
-    unsigned *cnt = h.lcnt.as<unsigned>();
+    FMM_TRY(lcnt.reserve((size_t)(nc + 1) * sizeof(unsigned)));
+    FMM_TRY(lkeys.reserve(std::max<int64_t>(n, 1) * sizeof(int)));
+    unsigned *cnt = lcnt.as<unsigned>();
     unsigned *offu = reinterpret_cast<unsigned *>(off.as<int>());
-    FMM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nc + 1) * sizeof(unsigned), h.stream));
+    FMM_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nc + 1) * sizeof(unsigned), stream));
     const int gb = L.nreg;   // one block per region
     if (n > 0) {
         ++h.launches;
-        k_list_count<<<gb, 256, 0, h.stream>>>(L, cnt, pcnt, pairs_total);
+        k_list_count<<<gb, 256, 0, stream>>>(L, cnt, pcnt, pairs_total);
     }
-    FMM_TRY(scan_exclusive_u32(h, cnt, offu, nc + 1, nullptr));
+    FMM_TRY(scan_exclusive_u32_on(h, stream, scan_tmp, cnt, offu, nc + 1, nullptr));
     if (n > 0) {
         ++h.launches;
-        k_list_scatter<<<gb, 256, 0, h.stream>>>(L, offu, cnt, h.lkeys.as<int>());
+        k_list_scatter<<<gb, 256, 0, stream>>>(L, offu, cnt, lkeys.as<int>());
         ++h.launches;
-        k_list_segsort<<<ceil_div((int64_t)nc * 32, kSegWarps * 32), kSegWarps * 32, 0, h.stream>>>(
-            nc, offu, h.lkeys.as<int>(), src.as<int>(), &h.counters.as<TravCounters>()->seg_long, bit);
+        k_list_segsort<<<ceil_div((int64_t)nc * 32, kSegWarps * 32), kSegWarps * 32, 0, stream>>>(
+            nc, offu, lkeys.as<int>(), src.as<int>(), &h.counters.as<TravCounters>()->seg_long, bit);
     }
     FMM_CHECK_LAUNCH("group list");
+    return FMM_OK;
+}
+
+// The M2L list is grouped on the handle's second stream (created on first
+// use), beside the P2P list, the mutual split and the work items.
+// join_lists_begin makes the handle's stream wait for it and copies its flag
+// to the host; join_lists_end (after the stream is synchronised) regroups the
+// list by radix sort if it repeats a pair.
+static int side_stream(Handle &h)
+{
+    if (h.side) return FMM_OK;
+    FMM_CUDA(cudaStreamCreateWithFlags(&h.side, cudaStreamNonBlocking));
+    FMM_CUDA(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
+    FMM_CUDA(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
+    return FMM_OK;
+}
+
+int join_lists_begin(Handle &h)
+{
+    if (!h.side_pending) return FMM_OK;
+    FMM_CUDA(cudaStreamWaitEvent(h.stream, h.ev_join, 0));
+    TravCounters *ctr = h.counters.as<TravCounters>();
+    FMM_CUDA(cudaMemcpyAsync(&h.pinned->ctr.seg_long, &ctr->seg_long, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             h.stream));
+    return FMM_OK;
+}
+
+int join_lists_end(Handle &h)
+{
+    if (!h.side_pending) return FMM_OK;
+    h.side_pending = false;
+    if (h.pinned->ctr.seg_long & 1u) {
+        const RegionList lm2l = {h.m2l_raw.as<int2>(), h.trav_reg.as<unsigned>(), (unsigned)h.m2l_cap,
+                                 h.num_sms * kStackBlocksPerSM};
+        FMM_TRY(group_list_radix(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off));
+        FMM_CUDA(cudaStreamSynchronize(h.stream));
+    }
     return FMM_OK;
 }
 
@@ -788,17 +827,22 @@ int build_lists(Handle &h)
     const RegionList lp2p = {h.p2p_raw.as<int2>(), reg + nreg, (unsigned)h.p2p_cap, nreg};
     // the P2P particle-pair total (for the counters) comes with the P2P list's counts
     FMM_CUDA(cudaMemsetAsync(&ctr->p2p_pairs, 0, sizeof(unsigned long long), h.stream));
-    FMM_TRY(group_list(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off, 1u));
-    FMM_TRY(group_list(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off, 2u, h.c_pcnt.as<int>(), &ctr->p2p_pairs));
+    FMM_TRY(side_stream(h));
+    FMM_CUDA(cudaEventRecord(h.ev_fork, h.stream));
+    FMM_CUDA(cudaStreamWaitEvent(h.side, h.ev_fork, 0));
+    FMM_TRY(group_list(h, h.side, h.lcnt_side, h.lkeys_side, h.scan_tmp_side, lm2l, h.n_m2l, h.m2l_src, h.m2l_off,
+                       1u));
+    FMM_CUDA(cudaEventRecord(h.ev_join, h.side));
+    h.side_pending = true;
+    FMM_TRY(group_list(h, h.stream, h.lcnt, h.lkeys, h.scan_tmp, lp2p, h.n_p2p, h.p2p_src, h.p2p_off, 2u,
+                       h.c_pcnt.as<int>(), &ctr->p2p_pairs));
     FMM_CUDA(cudaMemcpyAsync(hc, ctr, sizeof(TravCounters), cudaMemcpyDeviceToHost, h.stream));
     FMM_CUDA(cudaStreamSynchronize(h.stream));
     h.p2p_pairs = (int64_t)hc->p2p_pairs;
     h.nleaves = hc->nleaves;
-    if (hc->seg_long) {
-        // a repeated (target, source) pair: regroup that list by radix sort
-        if (hc->seg_long & 1u) FMM_TRY(group_list_radix(h, lm2l, h.n_m2l, h.m2l_src, h.m2l_off));
-        if (hc->seg_long & 2u) FMM_TRY(group_list_radix(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off));
-    }
+    // a repeated (target, source) pair in the P2P list: regroup it by radix sort
+    // (the M2L list's flag is read when its stream is joined)
+    if (hc->seg_long & 2u) FMM_TRY(group_list_radix(h, lp2p, h.n_p2p, h.p2p_src, h.p2p_off));
     phase_end(h, FMM_PHASE_LISTS);
     return FMM_OK;
 }
