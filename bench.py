@@ -464,8 +464,13 @@ def variant_systems(torch, stream, flush):
         "graph_nodes": info["graph_nodes"], "p2p_targets_per_item": info["p2p_targets_per_item"],
         "autotune_near_field_ms": {"one_sided_16_targets": info["tune_ms"][0],
                                    "one_sided_8_targets": info["tune_ms"][1],
-                                   "mutual_16_targets": info["tune_ms"][2], "mutual_8_targets": info["tune_ms"][3]},
-        "autotune_choice": {"targets_per_item": info["p2p_targets_per_item"], "mutual": bool(info["mutual"])},
+                                   "mutual_2_per_lane_16_targets": info["tune_ms"][2],
+                                   "mutual_2_per_lane_8_targets": info["tune_ms"][3],
+                                   "mutual_4_per_lane_16_targets": info["tune_ms"][4],
+                                   "mutual_4_per_lane_8_targets": info["tune_ms"][5]},
+        "autotune_choice": {"targets_per_item": info["p2p_targets_per_item"],
+                            "near_field": ["one-sided", "mutual, 2 sources per lane",
+                                           "mutual, 4 sources per lane"][info["mutual"]]},
         "p2p_pairs": info["p2p_pairs"]}}
 
 

@@ -267,9 +267,10 @@ struct fmm_multi_info {
     int64_t kernel_launches;       /* kernels launched on the merged problem (merge, tuning, eager runs) */
     int32_t nsys, nlevels;
     int32_t p2p_targets_per_item;  /* the autotuner's choice (or the pinned one) */
-    int32_t mutual;                /* 1: the mutual near field was chosen (or pinned) */
-    double tune_ms[4];             /* near-field time: one-sided 16, one-sided 8, mutual 16, mutual 8 targets
-                                      per item (best of 3 each) */
+    int32_t mutual;                /* 0: one-sided near field; 1 / 2: mutual with 2 / 4 staged sources per lane
+                                      (the autotuner's choice or the pinned one) */
+    double tune_ms[6];             /* near-field time with 16 / 8 targets per item: one-sided 16, 8; mutual
+                                      (2 per lane) 16, 8; mutual (4 per lane) 16, 8 (best of 3 each) */
     double ms_evaluate;            /* device time of the last graph replay */
 };
 
@@ -299,8 +300,10 @@ int fmm_multi_set_hybrid(fmm_multi *m, int64_t min_pairs);
 /*
  * fmm_multi_set_config -- pin the near-field configuration instead of letting
  * the autotuner choose: targets_per_item 0 (tune), 8 or 16; mutual -1 (tune),
- * 0 (one-sided) or 1 (mutual).  Applied at the next fmm_multi_evaluate (the
- * table is still timed and reported by fmm_multi_info).
+ * 0 (one-sided), 1 (mutual, 2 staged sources per lane, 12 warps per SM) or 2
+ * (mutual, 4 staged sources per lane, 8 warps per SM).  Applied at the next
+ * fmm_multi_evaluate (the table is still timed and reported by fmm_multi_info).
+ * FMM_ERR_ARG for any other value.
  */
 int fmm_multi_set_config(fmm_multi *m, int targets_per_item, int mutual);
 

@@ -164,6 +164,7 @@ struct Handle {
     // (B > A, mirrored) and one-sided ones (CSR by cell), their source runs, and
     // the accumulator of the mutual pass (float4 per sorted particle)
     bool mutual_ready = false;
+    int mu_lanes = 2;               // staged sources per lane of the mutual pass: 2 (6 blocks / SM) or 4 (4 blocks / SM)
     bool full_runs_ready = false;   // the whole lists' runs (p2p_poff / ent / cnt) are built
     DevBuf mu_off, mu_src, os_off, os_src, mu_cnt_tmp;
     DevBuf mu_poff, mu_ent, mu_cnt, os_poff, os_ent, os_cnt;

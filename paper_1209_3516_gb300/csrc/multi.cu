@@ -10,9 +10,10 @@
 // one M2L and one P2P launch in total, whatever the number of systems.
 // That evaluation is captured into a CUDA graph once and replayed, so a call
 // costs one graph launch.  Before capture an autotuner times the near field on
-// the merged problem in four configurations -- work items of 16 or 8 targets,
-// one-sided or mutual (each unordered leaf pair once, both directions) -- and
-// keeps the fastest (fmm_multi_set_config can pin either choice).
+// the merged problem in six configurations -- work items of 16 or 8 targets;
+// one-sided, or mutual (each unordered leaf pair once, both directions) with 2
+// or 4 staged sources per lane -- and keeps the fastest (fmm_multi_set_config
+// can pin any choice).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -110,8 +111,8 @@ struct Multi {
     float *g_phi = nullptr, *g_grad = nullptr;
     bool merged = false, tuned = false, timed = false;
     // P2P phase time per configuration: one-sided with 16 / 8 targets per item,
-    // mutual with 16 / 8 (the autotuner's table)
-    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
+    // mutual (2 sources per lane) with 16 / 8, mutual (4 sources per lane) with 16 / 8 (the autotuner's table)
+    float tune_ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int pin_g = 0, pin_mutual = -1;   // fmm_multi_set_config (0 / -1: tune)
     int64_t n_m2l = 0, p2p_pairs = 0;
 };
@@ -302,16 +303,19 @@ static int time_p2p(Multi &m, float *phi, float *grad, float *best_ms)
 }
 
 // The tile autotuner of the merged problem (the far field of this call is in
-// place): the near field with work items of 16 and of 8 targets, one-sided
-// and mutual, each timed on the merged problem; the fastest is kept, unless
-// fmm_multi_set_config pinned a choice.
+// place): the near field with work items of 16 and of 8 targets, one-sided,
+// mutual with 2 staged sources per lane (12 warps per SM) and mutual with 4
+// (8 warps per SM), each timed on the merged problem; the fastest is kept,
+// unless fmm_multi_set_config pinned a choice.
 static int autotune(Multi &m, float *phi, float *grad)
 {
     Handle &hm = m.hm;
     const int gs[2] = {16, 8};
-    for (int mu = 0; mu < 2; ++mu) {
-        if (mu) FMM_TRY(build_mutual(hm));
+    const int lanes[3] = {0, 2, 4};   // mode 0 one-sided, 1 / 2 mutual with that many sources per lane
+    for (int mu = 0; mu < 3; ++mu) {
+        if (mu == 1) FMM_TRY(build_mutual(hm));
         hm.mutual_ready = mu != 0;
+        if (mu) hm.mu_lanes = lanes[mu];
         for (int k = 0; k < 2; ++k) {
             hm.p2p_g = gs[k];
             FMM_TRY(build_work_items(hm, gs[k], hm.p2p_items, hm.n_items));
@@ -319,12 +323,13 @@ static int autotune(Multi &m, float *phi, float *grad)
         }
     }
     int best = 0;
-    for (int i = 1; i < 4; ++i)
+    for (int i = 1; i < 6; ++i)
         if (m.tune_ms[i] < m.tune_ms[best]) best = i;
     int mu = best >> 1, g = gs[best & 1];
     if (m.pin_mutual >= 0) mu = m.pin_mutual;
     if (m.pin_g) g = m.pin_g;
     hm.mutual_ready = mu != 0;
+    if (mu) hm.mu_lanes = lanes[mu];
     hm.p2p_g = g;
     FMM_TRY(build_work_items(hm, g, hm.p2p_items, hm.n_items));
     m.tuned = true;
@@ -562,8 +567,8 @@ int fmm_multi_set_config(fmm_multi *w, int targets_per_item, int mutual)
         set_error("fmm_multi_set_config: targets_per_item must be 0 (tune), 8 or 16");
         return FMM_ERR_ARG;
     }
-    if (mutual < -1 || mutual > 1) {
-        set_error("fmm_multi_set_config: mutual must be -1 (tune), 0 or 1");
+    if (mutual < -1 || mutual > 2) {
+        set_error("fmm_multi_set_config: mutual must be -1 (tune), 0, 1 or 2");
         return FMM_ERR_ARG;
     }
     w->m.pin_g = targets_per_item;
@@ -588,8 +593,8 @@ int fmm_multi_info(fmm_multi *w, struct fmm_multi_info *info)
     info->n_m2l = m.n_m2l;
     info->p2p_pairs = m.p2p_pairs;
     info->p2p_targets_per_item = m.hm.p2p_g ? m.hm.p2p_g : 16;
-    info->mutual = m.hm.mutual_ready ? 1 : 0;
-    for (int i = 0; i < 4; ++i) info->tune_ms[i] = m.tune_ms[i];
+    info->mutual = m.hm.mutual_ready ? (m.hm.mu_lanes == 4 ? 2 : 1) : 0;
+    for (int i = 0; i < 6; ++i) info->tune_ms[i] = m.tune_ms[i];
     info->graph_nodes = (int64_t)m.graph_nodes;
     info->kernel_launches = m.hm.launches;
     if (m.timed) {

@@ -162,7 +162,10 @@ constexpr int kMuSmem = (kMuThreads / 32) * (4 * kMuSlots + kMuG) * (int)sizeof(
 #ifndef FMM_MU_PER_LANE
 #define FMM_MU_PER_LANE 2
 #endif
-constexpr int kMuPerLane = FMM_MU_PER_LANE;   // staged sources per lane per step
+constexpr int kMuPerLane = FMM_MU_PER_LANE;   // staged sources per lane per step (the default shape)
+// The second shape the many-systems autotuner tries: 4 staged sources per
+// lane at 4 blocks per SM.
+constexpr int kMuPerLaneWide = 4, kMuMinBlocksWide = 4;
 #ifndef FMM_MU_MIN_BLOCKS
 #define FMM_MU_MIN_BLOCKS 6
 #endif
@@ -266,7 +269,7 @@ __device__ __forceinline__ void mu_tile(const float4 *s, const float2 *ntx_r, co
     }
 }
 
-template <int NT>
+template <int NT, int U>
 __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, const int *run_end, const float4 *pos,
                                           float4 *buf, const float2 *ntx, const float2 *nty, const float2 *ntz,
                                           const float2 *nqt, const float4 *tsm, float2 *acc, float4 *racc)
@@ -283,13 +286,13 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
         cp_async_wait_1();
         __syncwarp();
 #pragma unroll 1
-        for (int t0 = 0; t0 < n_cur; t0 += 32 * kMuPerLane) {
-            // kMuPerLane staged sources per lane per step: independent chains side by side
-            float4 s[kMuPerLane];
-            int sidx[kMuPerLane];
-            float2 ps[kMuPerLane], gsx[kMuPerLane], gsy[kMuPerLane], gsz[kMuPerLane];
+        for (int t0 = 0; t0 < n_cur; t0 += 32 * U) {
+            // U staged sources per lane per step: independent chains side by side
+            float4 s[U];
+            int sidx[U];
+            float2 ps[U], gsx[U], gsy[U], gsz[U];
 #pragma unroll
-            for (int u = 0; u < kMuPerLane; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int j = t0 + 32 * u + lane;
                 s[u] = make_float4(1e20f, 1e20f, 1e20f, 0.f);   // past the count: far away, no charge
                 sidx[u] = -1;
@@ -303,9 +306,9 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
                 }
                 ps[u] = gsx[u] = gsy[u] = gsz[u] = make_float2(0.f, 0.f);
             }
-            mu_tile<NT, kMuPerLane>(s, ntx, nty, ntz, nqt, tsm, acc, ps, gsx, gsy, gsz);
+            mu_tile<NT, U>(s, ntx, nty, ntz, nqt, tsm, acc, ps, gsx, gsy, gsz);
 #pragma unroll
-            for (int u = 0; u < kMuPerLane; ++u)
+            for (int u = 0; u < U; ++u)
                 if (sidx[u] >= 0)
                     red_add_v4(racc + sidx[u], -(ps[u].x + ps[u].y), gsx[u].x + gsx[u].y, gsy[u].x + gsy[u].y,
                                gsz[u].x + gsz[u].y);
@@ -315,8 +318,10 @@ __device__ __forceinline__ void mu_stream(RunCursor &cur, const float4 *run, con
     }
 }
 
-// One warp per work item (<= 16 targets of a leaf) over its mutual runs.
-__global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
+// One warp per work item (<= 16 targets of a leaf) over its mutual runs, U
+// staged sources per lane per step.
+template <int U, int MinBlocks>
+__global__ void __launch_bounds__(kMuThreads, MinBlocks)
     k_p2p_mutual(int nitems, const int4 *items, const unsigned *roff, const float4 *run, const int *run_end,
                  const float4 *pos, float4 *racc)
 {
@@ -359,10 +364,10 @@ __global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < 2 * kMuG; ++i) a[i] = make_float2(0.0f, 0.0f);
     const int ntr = tc <= 4 ? 4 : tc <= 8 ? 8 : tc <= 12 ? 12 : 16;
-    if (ntr == 4) mu_stream<4>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
-    else if (ntr == 8) mu_stream<8>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
-    else if (ntr == 12) mu_stream<12>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
-    else mu_stream<16>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    if (ntr == 4) mu_stream<4, U>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else if (ntr == 8) mu_stream<8, U>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else if (ntr == 12) mu_stream<12, U>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
+    else mu_stream<16, U>(cur, run, run_end, pos, buf, ntx, nty, ntz, nqt, tsm, a, racc);
     // target side: reduce-scatter, lanes 2g / 2g + 1 add (phi, gx) / (gy, gz) of target g
     float v[64];
 #pragma unroll
@@ -379,20 +384,27 @@ __global__ void __launch_bounds__(kMuThreads, FMM_MU_MIN_BLOCKS)
     if (g < tc) red_add_v2(reinterpret_cast<float *>(racc + tb + g) + 2 * (lane & 1u), v[0], v[1]);
 }
 
-int p2p_mutual(Handle &h)
+template <int U, int MinBlocks> static int p2p_mutual_launch(Handle &h)
 {
     static bool configured[64] = {};
     if (h.device >= 0 && h.device < 64 && !configured[h.device]) {
-        FMM_CUDA(cudaFuncSetAttribute(k_p2p_mutual, cudaFuncAttributeMaxDynamicSharedMemorySize, kMuSmem));
+        FMM_CUDA(cudaFuncSetAttribute(k_p2p_mutual<U, MinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kMuSmem));
         configured[h.device] = true;
     }
     FMM_CUDA(cudaMemsetAsync(h.racc.p, 0, (size_t)h.N * sizeof(float4), h.stream));
     ++h.launches;
-    k_p2p_mutual<<<ceil_div((int64_t)h.n_items * 32, kMuThreads), kMuThreads, kMuSmem, h.stream>>>(
+    k_p2p_mutual<U, MinBlocks><<<ceil_div((int64_t)h.n_items * 32, kMuThreads), kMuThreads, kMuSmem, h.stream>>>(
         (int)h.n_items, h.p2p_items.as<int4>(), h.mu_poff.as<unsigned>(), h.mu_ent.as<float4>(), h.mu_cnt.as<int>(),
         h.pos.as<float4>(), h.racc.as<float4>());
     FMM_CHECK_LAUNCH("mutual p2p");
     return FMM_OK;
+}
+
+int p2p_mutual(Handle &h)
+{
+    if (h.mu_lanes == kMuPerLaneWide) return p2p_mutual_launch<kMuPerLaneWide, kMuMinBlocksWide>(h);
+    return p2p_mutual_launch<kMuPerLane, FMM_MU_MIN_BLOCKS>(h);
 }
 
 }  // namespace fmm

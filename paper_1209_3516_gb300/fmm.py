@@ -60,7 +60,7 @@ class _MultiInfo(ctypes.Structure):
                 ("n_m2l", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("nsys", ctypes.c_int32), ("nlevels", ctypes.c_int32),
                 ("p2p_targets_per_item", ctypes.c_int32), ("mutual", ctypes.c_int32),
-                ("tune_ms", ctypes.c_double * 4), ("ms_evaluate", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double * 6), ("ms_evaluate", ctypes.c_double)]
 
 
 _lib = None
@@ -415,12 +415,13 @@ class MultiFMM:
         return phi, grad
 
     def set_config(self, targets_per_item=0, mutual=-1):
-        """fmm_multi_set_config: pin the near field (0 / -1 let the autotuner choose)."""
+        """fmm_multi_set_config: pin the near field (0 / -1 let the autotuner choose; mutual 0 one-sided,
+        1 / 2 mutual with 2 / 4 staged sources per lane)."""
         _check(load().fmm_multi_set_config(self._h, int(targets_per_item), int(mutual)))
 
     def info(self) -> dict:
         i = _MultiInfo()
         _check(load().fmm_multi_info(self._h, ctypes.byref(i)))
         d = {k: getattr(i, k) for k, _ in _MultiInfo._fields_ if k not in ("tune_ms", "reserved")}
-        d["tune_ms"] = [i.tune_ms[k] for k in range(4)]
+        d["tune_ms"] = [i.tune_ms[k] for k in range(6)]
         return d

@@ -164,7 +164,7 @@ def test_multi_with_hybrid(torch_cuda):
     m.close()
 
 
-@pytest.mark.parametrize("g,mutual", [(16, 0), (8, 0), (16, 1), (8, 1)])
+@pytest.mark.parametrize("g,mutual", [(16, 0), (8, 0), (16, 1), (8, 1), (16, 2), (8, 2)])
 def test_multi_every_tile_configuration(torch_cuda, g, mutual):
     # each configuration the autotuner may choose, pinned: every system against its oracle
     sizes = [5000, 40, 11000, 900, 3001]
