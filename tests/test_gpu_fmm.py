@@ -599,3 +599,30 @@ def test_large_n_16m(torch_cuda):
           % (e[0], e[1], st["ncells"], st["nlevels"], st["n_m2l"], st["n_p2p"], st["p2p_pairs"]))
     assert e[0] < 5e-3 and e[1] < 5e-3   # P = 4, theta = 0.5 accuracy (1.3e-3 / 6.4e-4 at N = 1M)
     h.close()
+
+
+def test_build_deterministic(torch_cuda):
+    # the traversal's pairs land in per-block regions in an order that changes
+    # from run to run, and the M2L list is grouped on a second stream: the
+    # grouped lists, the sorted particles and a one-sided evaluation from them
+    # must still be the same, bit for bit, build after build (adaptive tree:
+    # several work-stack passes; all three list kinds non-trivial)
+    torch = torch_cuda
+    from paper_1209_3516_gb300 import fmm
+    N = 262144
+    x, q = inputs.plummer(N, inputs.SEED_BASE + 11)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    qd = torch.from_numpy(q.astype(np.float32)).cuda()
+    h = fmm.FMM(N, 4, 0.4, 32)
+    runs = []
+    for _ in range(3):
+        h.build(xd)
+        phi, grad = h.evaluate(qd)
+        torch.cuda.synchronize()
+        keys, perm = h.sorted()
+        m, p = h.lists()
+        runs.append((keys, perm, m, p, phi.cpu().numpy(), grad.cpu().numpy()))
+    h.close()
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)
