@@ -274,10 +274,19 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const K *keys, const 
 // Every wait of the look-back is bounded; a wait that gives up sets bit 8 of
 // the error word (the build then fails instead of hanging).
 // ---------------------------------------------------------------------------
-constexpr int kOsThreads = 512;                         // threads 0..255 also own one digit each
+// Tile shape (N = 1M, Morton sort phase): 256 x 16 keys 0.276 ms, 512 x 8 0.266,
+// 512 x 16 (spills) 0.259, 1024 x 8 0.252: fewer, larger tiles shorten the
+// look-back chain.
+#ifndef FMM_OS_THREADS
+#define FMM_OS_THREADS 1024
+#endif
+constexpr int kOsThreads = FMM_OS_THREADS;              // threads 0..255 also own one digit each
 constexpr int kOsWarps = kOsThreads / 32;
-constexpr int kOsPerThread = 8;                         // keys per thread
-constexpr int kOsTile = kOsThreads * kOsPerThread;      // 4096 keys per tile
+#ifndef FMM_OS_PER_THREAD
+#define FMM_OS_PER_THREAD 8
+#endif
+constexpr int kOsPerThread = FMM_OS_PER_THREAD;         // keys per thread
+constexpr int kOsTile = kOsThreads * kOsPerThread;      // keys per tile (8192)
 constexpr unsigned kOsAgg = 1u << 30, kOsPrefix = 2u << 30, kOsValue = (1u << 30) - 1u;
 constexpr int kOsSpinMax = 1 << 20;   // look-back windows without progress before giving up
 constexpr int kOsWindow = 16;          // predecessors read per look-back window
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_hist(const K *keys, int64_t n
 }
 
 template <class K, bool kVals>
-__global__ void __launch_bounds__(kOsThreads, 2) k_os_pass(const K *keys, const unsigned *vals, int64_t n, int shift,
+__global__ void __launch_bounds__(kOsThreads, 1024 / kOsThreads) k_os_pass(const K *keys, const unsigned *vals, int64_t n, int shift,
                                                         const unsigned *ghist, unsigned *status, unsigned *tile_ctr,
                                                         K *keys_out, unsigned *vals_out, unsigned *err)
 {
