@@ -2,8 +2,10 @@
 //
 // The paper's method descends from falcON (Sec. 2), whose near field evaluates
 // every pair of leaves once and applies the interaction to both of them.  The
-// P2P lists that Algorithm 4 emits here are symmetric ((A, B) is listed iff
-// (B, A) is), so with FMM_FLAG_MUTUAL each target leaf's list is split into
+// P2P lists that Algorithm 4 emits here are symmetric in practice ((A, B) is
+// listed iff (B, A) is; the split rule can break this when two cells have
+// equal radii, so every mirror is checked), and with FMM_FLAG_MUTUAL each
+// target leaf's list is split into
 //   - its mutual part: sources B > A whose mirror entry (B, A) exists, and
 //   - its one-sided part: B == A, and any entry without a mirror (checked by
 //     a binary search for A in B's sorted list from the entry with B > A; none
@@ -35,37 +37,58 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 // list split
 // ---------------------------------------------------------------------------
-// Position of a in the sorted list src[b0, b1), or -1.
-__device__ __forceinline__ int list_find(const int *src, int b0, int b1, int a)
-{
-    while (b0 < b1) {
-        const int m = (b0 + b1) >> 1;
-        const int v = src[m];
-        if (v == a) return m;
-        if (v < a) b0 = m + 1;
-        else b1 = m;
-    }
-    return -1;
-}
-
 // Entry kinds (one byte per list entry, preset to 2): 0 skip (the mirror's
 // mutual entry covers it), 1 mutual, 2 one-sided.  One warp per leaf A; each
-// entry B > A looks A up in B's list: found, the entry is mutual and its
-// mirror is skipped; not found, both stay one-sided.  Entries B == A, and
-// B < A whose mirror was not found, stay one-sided.
+// entry B > A looks A up in B's sorted list by binary search: found, the entry
+// is mutual and its mirror is skipped; not found, both stay one-sided.
+// Entries B == A, and B < A whose mirror was not found, stay one-sided.  Each
+// lane runs the searches of two entries (e and e + 32) in lockstep, so that
+// their dependent loads overlap.
 __global__ void k_mutual_mark(int nleaves, const int *leaf_list, const int *off, const int *src, unsigned char *kind)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nleaves) return;
     const int t = leaf_list[w];
     const int eb = off[t], ee = off[t + 1];
-    for (int e = eb + (int)lane_id(); e < ee; e += 32) {
-        const int b = src[e];
-        if (b <= t) continue;
-        const int m = list_find(src, off[b], off[b + 1], t);
-        if (m >= 0) {
+    for (int e = eb + (int)lane_id(); e < ee; e += 64) {
+        const int e2 = e + 32;
+        const int b1 = src[e], b2 = e2 < ee ? src[e2] : -1;
+        // [lo, hi) search ranges; an empty range for an entry that does not search
+        int lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+        if (b1 > t) {
+            lo1 = off[b1];
+            hi1 = off[b1 + 1];
+        }
+        if (b2 > t) {
+            lo2 = off[b2];
+            hi2 = off[b2 + 1];
+        }
+        int m1 = -1, m2 = -1;
+        while (lo1 < hi1 || lo2 < hi2) {
+            const int c1 = (lo1 + hi1) >> 1, c2 = (lo2 + hi2) >> 1;
+            const int v1 = lo1 < hi1 ? src[c1] : 0, v2 = lo2 < hi2 ? src[c2] : 0;
+            if (lo1 < hi1) {
+                if (v1 == t) {
+                    m1 = c1;
+                    hi1 = lo1;
+                } else if (v1 < t) lo1 = c1 + 1;
+                else hi1 = c1;
+            }
+            if (lo2 < hi2) {
+                if (v2 == t) {
+                    m2 = c2;
+                    hi2 = lo2;
+                } else if (v2 < t) lo2 = c2 + 1;
+                else hi2 = c2;
+            }
+        }
+        if (m1 >= 0) {
             kind[e] = 1;
-            kind[m] = 0;
+            kind[m1] = 0;
+        }
+        if (m2 >= 0) {
+            kind[e2] = 1;
+            kind[m2] = 0;
         }
     }
 }
